@@ -1,0 +1,343 @@
+"""Benchmark of the MPHF query path (one JSON line on rank 0).
+
+Workload: n = 1e9 distinct u64 keys (seeded), Default parameters (gamma_3,
+lambda 3.5, alpha 0.99, CacheLineEF), structure built on the GPU by the
+library; one step = one query of all n keys in a seeded random order
+(8 GB of keys in, 4 GB of u32 out, inputs far larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n N] [--impl reference]
+
+--impl reference times the CPU oracle (one-by-one queries on the host
+cores) on a bounded sample of the same workload.  Under torchrun every rank
+holds a full replica and queries its own n keys (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPHF ns/key & queries/s at n=1e9 u64; % of random-gather roofline; p99 lat"
+UNIT = "queries/s"
+QUERY_KERNEL_SOURCES = ["paper_2502_15539_gb300/csrc/mphf_query.cu", "paper_2502_15539_gb300/csrc/mphf_internal.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "query_u64_kernel_n1e9.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=float, default=1e9)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=1 << 26, help="oracle baseline sample (keys)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in QUERY_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[float, str]:
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(n: int):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source for this n; else None."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    sha = re.search(r"kernel_source_sha:\s*(\w+)", text)
+    bpk = re.search(r"dram_bytes_per_key:\s*([0-9.]+)", text)
+    if not sha or not bpk or sha.group(1) != kernel_source_sha():
+        return None
+    return float(bpk.group(1)) * n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self) -> dict:
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        busy = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)]
+        return {"sm_mhz": statistics.median(busy or sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_15539_gb300 import build_ext
+    from paper_2502_15539_gb300 import native as N
+    from paper_2502_15539_gb300 import workloads as W
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or not os.path.exists(N.LIB_PATH):
+        build_ext.build()
+    if ws > 1:
+        dist.barrier()
+    N.load()
+    n = int(args.n)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    keys = W.u64_keys(n, seed=0, device=dev)
+    m = N.mphf_build(keys)
+    info = N.mphf_info(m)
+    perm = W.permutation(n, seed=1 + rank, device=dev)
+    q = keys[perm]
+    del perm
+    torch.cuda.empty_cache()
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # Fraction of keys whose slot is >= n (they read one CacheLineEF line).
+    N.mphf_query_u64_phf(m, q, out)
+    remapped = int(((out.to(torch.int64) & 0xFFFFFFFF) >= n).sum().item())
+    del keys
+    torch.cuda.empty_cache()
+
+    def time_steps(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        barrier()
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        barrier()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    run_query = lambda: N.mphf_query_u64(m, q, out, stream=stream)
+    for _ in range(args.warmup):
+        run_query()
+    launches0 = N.mphf_launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        per_step = time_steps(run_query, args.steps)
+        t1.record(stream)
+        barrier()
+    launches = N.mphf_launch_count() - launches0
+    clocks = clk.summary()
+    total_ms = sum(per_step)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n * args.steps / (total_ms / 1e3)
+
+    # Random-gather probe: same key stream, table the size of the pilot array.
+    table = torch.randint(0, 256, (info["pilot_bytes"],), dtype=torch.uint8, device=dev)
+    run_probe = lambda: N.mphf_gather_probe(q, table, out, stream=stream)
+    for _ in range(args.warmup):
+        run_probe()
+    probe_ms = statistics.mean(time_steps(run_probe, args.steps))
+    del table
+
+    # Roofline of the query kernel (HBM bound): algorithmic bytes per key =
+    # 8 (key) + 4 (result) + 32 (the pilot's DRAM sector) + 64 per remapped key.
+    peak, peak_kind = measured_peaks()
+    alg_bytes = n * (8 + 4 + 32) + remapped * 64
+    kernel_ms = statistics.mean(per_step)
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    traffic = recorded_traffic(n)
+
+    # End to end through the C ABI with pinned host buffers.
+    e2e = None
+    if not args.no_e2e:
+        qh = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        qh.copy_(q)
+        oh = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        for _ in range(max(1, args.warmup)):
+            N.mphf_query_u64_host(m, qh, oh)
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            N.mphf_query_u64_host(m, qh, oh)
+        barrier()
+        e2e_s = time.perf_counter() - w0
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": ws * n * args.steps / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n,
+               "ms_per_step": 1e3 * float(tt.item()) / args.steps}
+        del qh, oh
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(m, q, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"plain at scale: n={n} distinct u64 keys, query all n in a seeded random order",
+                       "n": n, "params": "Default (gamma_3, lambda 3.5, alpha 0.99, CacheLineEF)",
+                       "P": info["P"], "S": info["S"], "B": info["B"], "bits_per_key": info["bits_per_key"],
+                       "l2": "inputs larger than L2 (8 GB keys + 4 GB out per step, 286 MB pilots)",
+                       "parallelism": f"replicas x{ws}"},
+            "ns_per_key": 1e9 / (value / ws),
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "alg_bytes_per_key": alg_bytes / n,
+                         "kernel": "query_u64_kernel"},
+            "gather_roofline": {"probe_ms": probe_ms, "query_ms": kernel_ms, "frac": probe_ms / kernel_ms,
+                                "probe": "mphf_gather_probe: same key stream, 1 random byte of a "
+                                         f"{info['pilot_bytes']}-byte table per key"},
+            "remapped_fraction": remapped / n,
+            "build": {"ms": info["build_ms"], "ns_per_key": 1e6 * info["build_ms"] / n,
+                      "evictions": info["evictions"]},
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(m, q, sample: int):
+    """The oracle, as it stands, on the host cores: one-by-one queries of a
+    prefix of the same query stream against the same structure."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2502_15539_gb300 import native as N
+    from paper_2502_15539_gb300 import workloads as W
+
+    ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
+    cnt = min(sample, q.numel())
+    keys = W.as_uint64_numpy(q[:cnt])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref.query_u64(keys, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": cnt / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {cnt} keys of the query stream, same structure, {cores} threads"}
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2502_15539_gb300 import workloads as W
+
+    n = int(args.n)
+    cores = os.cpu_count() or 1
+    torch.set_num_threads(cores)
+    keys = W.as_uint64_numpy(W.u64_keys(n, seed=0))
+    ref = O.OracleMPHF.build_u64(keys, threads=cores)
+    del keys
+    sample = min(int(args.cpu_sample), n)
+    # A seeded sample of the query stream: keys of random indices.
+    idx = W.uniform_index(sample, n, seed=1)
+    qs = W.as_uint64_numpy(W.u64_keys_at(idx, seed=0))
+    for _ in range(args.warmup):
+        ref.query_u64(qs, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ref.query_u64(qs, threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"plain at scale: n={n} distinct u64 keys, query all n in a seeded random order",
+                   "n": n, "params": "Default (gamma_3, lambda 3.5, alpha 0.99, CacheLineEF)"},
+        "ns_per_key": 1e9 / value,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} keys drawn from the n-key query stream per step, "
+                                   f"oracle-built structure, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

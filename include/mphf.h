@@ -1,0 +1,190 @@
+/*
+ * mphf.h -- C ABI of the GB300-native PtrHash library (libmphf.so).
+ *
+ * PtrHash (Groot Koerkamp, SEA 2025) is a minimal perfect hash function: it
+ * maps a set of n distinct keys bijectively onto [0, n).  The structure is
+ * an array of 8-bit pilots, one per bucket, with P parts of B buckets and S
+ * slots each, plus one remap table for slots >= n (Sec. 3.1, Fig. overview).
+ *
+ * Conventions for every entry point below:
+ *  - Return 0 (MPHF_OK) or a negative MPHF_ERR_* code.  Nothing aborts and
+ *    no C++ exception crosses this boundary.  mphf_last_error() gives a
+ *    human-readable detail of the most recent failure on the calling thread.
+ *  - "device pointer" means memory of the current CUDA device, owned by the
+ *    caller, which must stay valid until the work on `stream` completes.
+ *    "host pointer" means ordinary host memory owned by the caller; host
+ *    memory that is page-locked (cudaHostAlloc / pinned) copies fastest.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Query calls are asynchronous on that stream unless stated.
+ *  - A structure (mphf_t) owns its device memory and is released with
+ *    mphf_free().  It may be queried concurrently from several streams.
+ *  - Integer arithmetic is exact; results are bit-identical to the formula
+ *    of Sec. 3.1 (Eq. partbucket, Eq. slot) and Sec. 3.4 (Eq. clef).
+ */
+#ifndef GB300_MPHF_H
+#define GB300_MPHF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- codes */
+#define MPHF_OK                 0
+#define MPHF_ERR_ARG           -1  /* invalid argument (NULL, size, alignment) */
+#define MPHF_ERR_OOM           -2  /* device or host allocation failed        */
+#define MPHF_ERR_DUP_KEYS      -3  /* the key set holds duplicates            */
+#define MPHF_ERR_BUILD_FAILED  -4  /* pilot search failed after every reseed  */
+#define MPHF_ERR_FORMAT        -5  /* serialized bytes are not a valid structure */
+#define MPHF_ERR_CUDA          -6  /* a CUDA runtime call failed              */
+#define MPHF_ERR_TIMEOUT       -7  /* a bounded device wait gave up           */
+#define MPHF_ERR_OVERFULL      -8  /* a part holds more keys than slots       */
+#define MPHF_ERR_CAPACITY      -9  /* a fixed capacity of the library exceeded */
+
+#define MPHF_KEY_U64    0  /* 64-bit integer keys, h(k) = C k (Sec. 3.1)       */
+#define MPHF_KEY_BYTES  1  /* byte strings: packed bytes + n+1 u64 offsets     */
+
+#define MPHF_GAMMA_LINEAR 1  /* gamma_1(x) = x                 (Sec. 3.3)     */
+#define MPHF_GAMMA_CUBIC  3  /* gamma_3, the Default          (Sec. 3.3)     */
+
+#define MPHF_REMAP_CLEF 0  /* CacheLineEF remap table         (Sec. 3.4)      */
+#define MPHF_REMAP_VEC  1  /* plain u32 remap table           (Sec. 3.4)      */
+
+/* ------------------------------------------------------------ parameters */
+/* Construction parameters (Sec. 3.1 "Parameter values", Sec. 4.1.2
+ * "Recommended parameters").  Default: lambda 3.5, alpha 0.99, gamma_3,
+ * CacheLineEF; Fast: lambda 3.0, gamma_1, Vec; Compact: lambda 4.0. */
+typedef struct {
+    double   lambda;          /* expected bucket size                         */
+    double   alpha;           /* load factor in (0, 1]                        */
+    int32_t  gamma;           /* MPHF_GAMMA_*                                 */
+    int32_t  remap;           /* MPHF_REMAP_*                                 */
+    uint64_t seed;            /* global seed of hp(p) = C (p xor seed), and of
+                                 the string hash                              */
+    uint64_t C;               /* odd 64-bit mixing constant                   */
+    uint64_t slots_override;  /* 0: the parameter rule picks S; else forced S */
+    int32_t  max_reseeds;     /* extra attempts with seed+1, seed+2, ...      */
+    uint32_t evict_mult;      /* a part fails after evict_mult * S evictions  */
+} mphf_params;
+
+/* Fills *p with the Default parameters.  Returns MPHF_ERR_ARG for NULL. */
+int mphf_default_params(mphf_params *p);
+
+typedef struct mphf mphf_t;
+
+/* Description of a structure. */
+typedef struct {
+    uint64_t n, P, S, B;      /* keys, parts, slots per part, buckets per part */
+    uint64_t C, seed;
+    int32_t  gamma, remap, reduce, key_kind;  /* reduce: 0 = hi(C x) mod 2^k,
+                                                 1 = x mod S (Sec. 3.1)      */
+    uint64_t remap_len;       /* P*S - n entries of the remap table F          */
+    uint64_t pilot_bytes;     /* P*B                                           */
+    uint64_t remap_bytes;     /* CacheLineEF: 64 per 44 entries; Vec: 4 each    */
+    double   bits_per_key;    /* 8 (pilot_bytes + remap_bytes) / n              */
+    uint64_t evictions;       /* hash-evict evictions of the build (0 if loaded)*/
+    double   build_ms;        /* device time of mphf_build (0 if loaded)        */
+} mphf_info_t;
+
+/* --------------------------------------------------------------- build */
+/* Builds the structure of n distinct keys on the GPU (Sec. 3.2: hash, sort,
+ * per-part greedy pilot search with hash-evict, then the remap of Sec. 3.4).
+ *   key_kind  MPHF_KEY_U64: keys_dev = n uint64_t (device pointer,
+ *             8-byte aligned); offsets_dev must be NULL.
+ *             MPHF_KEY_BYTES: keys_dev = packed bytes (device pointer);
+ *             offsets_dev = n+1 non-decreasing uint64_t (device), key i being
+ *             bytes [offsets[i], offsets[i+1]).
+ *   n         1 <= n < 2^32.
+ * Runs on `stream` and returns once the structure is complete (it
+ * synchronizes that stream).  Temporary device memory is allocated and freed
+ * inside.  Errors: MPHF_ERR_ARG, MPHF_ERR_DUP_KEYS (equal u64 keys, or equal
+ * strings), MPHF_ERR_OVERFULL, MPHF_ERR_BUILD_FAILED, MPHF_ERR_OOM,
+ * MPHF_ERR_CUDA.  On error *out is set to NULL. */
+int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
+               const uint64_t *offsets_dev, uint64_t n, void *stream,
+               mphf_t **out);
+
+/* ------------------------------------------------------------- queries */
+/* Evaluates the MPHF on m u64 keys (Sec. 3.1, Eq. partbucket and Eq. slot;
+ * Sec. 3.4 remap for slots >= n):
+ *   out[i] = slot(k_i) if slot(k_i) < n, else F[slot(k_i) - n].
+ * keys_dev: m uint64_t (device, 8-byte aligned; 16-byte alignment takes the
+ * vectorized path); out_dev: m uint32_t (device, 4-byte aligned).  Keys that
+ * are not members give a deterministic value in [0, n).  m = 0 is a no-op.
+ * Asynchronous on `stream`.  Errors: MPHF_ERR_ARG, MPHF_ERR_CUDA (launch). */
+int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
+                   uint32_t *out_dev, void *stream);
+
+/* The same for byte-string keys: key i = bytes_dev[offsets_dev[i] ..
+ * offsets_dev[i+1]).  offsets_dev: count+1 non-decreasing uint64_t (device).
+ * Requires a structure built for MPHF_KEY_BYTES (else MPHF_ERR_ARG). */
+int mphf_query_bytes(const mphf_t *m, const uint8_t *bytes_dev,
+                     const uint64_t *offsets_dev, uint64_t count,
+                     uint32_t *out_dev, void *stream);
+
+/* Perfect (non-minimal) hash: slot(k_i) in [0, P*S) without the remap
+ * (Sec. 3.1 Eq. slot; Table remap "Query PHF").  Same arguments as
+ * mphf_query_u64. */
+int mphf_query_u64_phf(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
+                       uint32_t *out_dev, void *stream);
+
+/* End-to-end query from host memory: copies the keys to the device in
+ * chunks, evaluates them and copies the results back, overlapping the
+ * copies with the kernels on `stream` and an internal copy stream.
+ * keys_host: count uint64_t (host); out_host: count uint32_t (host).
+ * Returns when every result is in out_host (synchronous).  Uses staging
+ * buffers owned by the structure (allocated on first use).  Errors:
+ * MPHF_ERR_ARG, MPHF_ERR_OOM, MPHF_ERR_CUDA. */
+int mphf_query_u64_host(mphf_t *m, const uint64_t *keys_host, uint64_t count,
+                        uint32_t *out_host, void *stream);
+
+/* ------------------------------------------------ serialize / describe */
+/* Serialized format (little-endian): a 128-byte header, the P*B pilot bytes
+ * padded to 64, then the remap payload.  This is the interchange format
+ * with other implementations.  With host_buf NULL or cap too small, only
+ * *needed is set and MPHF_ERR_ARG is returned if host_buf is not NULL.
+ * Synchronous. */
+int mphf_serialize(const mphf_t *m, void *host_buf, size_t cap, size_t *needed);
+
+/* Loads a serialized structure onto the current device (synchronous).
+ * Errors: MPHF_ERR_FORMAT (bad magic, version, sizes or fields),
+ * MPHF_ERR_OOM, MPHF_ERR_CUDA. */
+int mphf_deserialize(const void *host_buf, size_t len, mphf_t **out);
+
+int mphf_info(const mphf_t *m, mphf_info_t *out);
+
+/* Releases the structure and its device memory.  NULL is a no-op.  The
+ * caller must ensure no query on it is still running. */
+void mphf_free(mphf_t *m);
+
+const char *mphf_strerror(int code);
+
+/* Detail of the last failure on the calling thread (never NULL). */
+const char *mphf_last_error(void);
+
+/* Layout chosen by the parameter rule for n keys (Sec. 3.1 "Parameter
+ * values"), without building: fills P, S, B and reduce of *out. */
+int mphf_layout(const mphf_params *params, uint64_t n, mphf_info_t *out);
+
+/* ------------------------------------------------------ roofline probe */
+/* The random-gather microbenchmark that bounds the query kernel: for each
+ * of `count` u64 keys, one byte is read from table_dev[fastrange(mix(k),
+ * table_bytes)] and written out as u32, with the same key stream and the
+ * same launch shape as mphf_query_u64.  No paper counterpart: this is the
+ * measured denominator for the query kernel's roofline fraction.
+ * keys_dev: count u64 (device); table_dev: table_bytes bytes (device);
+ * out_dev: count u32 (device).  Asynchronous on `stream`. */
+int mphf_gather_probe(const uint64_t *keys_dev, uint64_t count,
+                      const uint8_t *table_dev, uint64_t table_bytes,
+                      uint32_t *out_dev, void *stream);
+
+/* Number of kernel launches this library issued since it was loaded
+ * (all entry points, all threads). */
+uint64_t mphf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

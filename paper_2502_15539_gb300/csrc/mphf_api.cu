@@ -1,0 +1,444 @@
+// C ABI of libmphf: structure handle, parameter rule, serialized format,
+// error reporting and the host-buffer query pipeline.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "mphf_internal.cuh"
+
+struct mphf {
+    ptrhash::Header hdr;
+    uint8_t *d_pilots = nullptr;
+    uint8_t *d_remap = nullptr;
+    int device = 0;
+    uint64_t evictions = 0;
+    double build_ms = 0.0;
+    // Staging for mphf_query_u64_host: two buffer sets, two copy streams.
+    std::mutex stage_mu;
+    uint64_t stage_chunk = 0;
+    uint64_t *d_stage_keys[2] = {nullptr, nullptr};
+    uint32_t *d_stage_out[2] = {nullptr, nullptr};
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_h2d[2] = {}, ev_q[2] = {}, ev_d2h[2] = {};
+};
+
+namespace ptrhash {
+
+static thread_local char g_err[512] = "no error";
+static std::atomic<uint64_t> g_launches{0};
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    if (e == cudaErrorMemoryAllocation) return MPHF_ERR_OOM;
+    return MPHF_ERR_CUDA;
+}
+
+void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
+
+// Sec. 3.1 "Parameter values": alpha S >= 80000 ln(n / 80000) keys per part
+// (at least 80000), S the smallest power of two that holds them, P =
+// ceil(n / (alpha S)), B = ceil(alpha S / lambda).  When that wastes more
+// than 5% of n/alpha slots (few parts), reduce becomes x mod S with P =
+// ceil(n / kpp), S = max(ceil(n / (alpha P)), ceil(n/P) + 16), S not a power
+// of two.  A forced S keeps P = ceil(n / (alpha S)).
+int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_override,
+                  uint64_t *P_out, uint64_t *S_out, uint64_t *B_out, int *reduce_out) {
+    if (n == 0 || n > 0xFFFFFFFFull || !(lambda > 0.0) || !(alpha > 0.0) || alpha > 1.0) {
+        set_error("invalid n=%llu, lambda=%g or alpha=%g", (unsigned long long)n, lambda, alpha);
+        return MPHF_ERR_ARG;
+    }
+    const double nd = (double)n;
+    const double keys_per_part = fmax(80000.0, 80000.0 * log(nd / 80000.0));
+    uint64_t S, P;
+    int reduce;
+    if (slots_override) {
+        S = slots_override;
+        P = (uint64_t)ceil(nd / (alpha * (double)S));
+        reduce = is_pow2(S) ? kReducePow2 : kReduceMod;
+    } else {
+        int k = 0;
+        while ((double)(1ull << k) < keys_per_part / alpha) k++;
+        S = 1ull << k;
+        P = (uint64_t)ceil(nd / (alpha * (double)S));
+        reduce = kReducePow2;
+        if ((double)(P * S) > 1.05 * nd / alpha) {
+            P = (uint64_t)ceil(nd / keys_per_part);
+            if (P == 0) P = 1;
+            S = (uint64_t)ceil(nd / (alpha * (double)P));
+            const uint64_t floor_s = (n + P - 1) / P + 16;
+            if (S < floor_s) S = floor_s;
+            if (is_pow2(S)) S++;
+            reduce = kReduceMod;
+        }
+    }
+    if (P == 0) P = 1;
+    uint64_t B = (uint64_t)ceil(alpha * (double)S / lambda);
+    if (B == 0) B = 1;
+    if (P * S < n || P * S > 0xFFFFFFFFull || B > 0xFFFFFFFEull) {
+        set_error("layout out of range: P=%llu S=%llu B=%llu", (unsigned long long)P,
+                  (unsigned long long)S, (unsigned long long)B);
+        return MPHF_ERR_ARG;
+    }
+    *P_out = P;
+    *S_out = S;
+    *B_out = B;
+    *reduce_out = reduce;
+    return MPHF_OK;
+}
+
+void fastmod_constant(uint64_t S, uint64_t *hi, uint64_t *lo) {
+    unsigned __int128 c = ~(unsigned __int128)0 / S + 1;   // ceil(2^128 / S), S not 2^k
+    *hi = (uint64_t)(c >> 64);
+    *lo = (uint64_t)c;
+}
+
+uint64_t clef_lines_for(uint64_t remap_len) { return (remap_len + kClefPerLine - 1) / kClefPerLine; }
+
+View make_view(const Header &h, const uint8_t *pilots, const void *remap) {
+    View v;
+    v.pilots = pilots;
+    v.remap = remap;
+    v.n = h.n; v.P = h.P; v.S = h.S; v.B = h.B; v.C = h.C; v.seed = h.seed;
+    v.s_mask = h.S - 1;
+    v.fm_hi = v.fm_lo = 0;
+    if (h.reduce == kReduceMod) fastmod_constant(h.S, &v.fm_hi, &v.fm_lo);
+    return v;
+}
+
+}  // namespace ptrhash
+
+using namespace ptrhash;
+
+// ------------------------------------------------------------- serialize
+// 128-byte little-endian header; see include/mphf.h.
+static void wr64(uint8_t *p, uint64_t v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static void wr32(uint8_t *p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static uint64_t rd64(const uint8_t *p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i); return v; }
+static uint32_t rd32(const uint8_t *p) { uint32_t v = 0; for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i); return v; }
+static uint64_t round64(uint64_t v) { return (v + 63) & ~63ull; }
+
+static const char kMagic[8] = {'P', 'T', 'R', 'H', 'A', 'S', 'H', '1'};
+
+extern "C" {
+
+int mphf_default_params(mphf_params *p) {
+    if (!p) { set_error("params is NULL"); return MPHF_ERR_ARG; }
+    memset(p, 0, sizeof(*p));
+    p->lambda = 3.5;
+    p->alpha = 0.99;
+    p->gamma = MPHF_GAMMA_CUBIC;
+    p->remap = MPHF_REMAP_CLEF;
+    p->seed = 0;
+    p->C = 0x9E3779B97F4A7C15ull;   // any odd constant; the paper prints none
+    p->slots_override = 0;
+    p->max_reseeds = 8;
+    p->evict_mult = 10;             // "a total of 10S evictions" (Sec. 4.1.2)
+    return MPHF_OK;
+}
+
+int mphf_layout(const mphf_params *params, uint64_t n, mphf_info_t *out) {
+    if (!params || !out) { set_error("NULL argument"); return MPHF_ERR_ARG; }
+    memset(out, 0, sizeof(*out));
+    uint64_t P, S, B;
+    int reduce;
+    int rc = choose_layout(n, params->lambda, params->alpha, params->slots_override, &P, &S, &B, &reduce);
+    if (rc) return rc;
+    out->n = n; out->P = P; out->S = S; out->B = B; out->reduce = reduce;
+    out->C = params->C; out->seed = params->seed; out->gamma = params->gamma; out->remap = params->remap;
+    out->remap_len = P * S - n;
+    out->pilot_bytes = P * B;
+    out->remap_bytes = params->remap == MPHF_REMAP_VEC ? 4 * out->remap_len : 64 * clef_lines_for(out->remap_len);
+    out->bits_per_key = 8.0 * (double)(out->pilot_bytes + out->remap_bytes) / (double)n;
+    return MPHF_OK;
+}
+
+int mphf_serialize(const mphf_t *m, void *host_buf, size_t cap, size_t *needed) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    const Header &h = m->hdr;
+    const uint64_t pb = h.P * h.B;
+    const uint64_t need = 128 + round64(pb) + h.remap_bytes;
+    if (needed) *needed = need;
+    if (!host_buf) return MPHF_OK;
+    if (cap < need) { set_error("buffer of %zu bytes, %llu needed", cap, (unsigned long long)need); return MPHF_ERR_ARG; }
+    int dev_prev = 0;
+    cudaGetDevice(&dev_prev);
+    cudaSetDevice(m->device);
+    uint8_t *b = (uint8_t *)host_buf;
+    memset(b, 0, 128 + round64(pb));
+    memcpy(b, kMagic, 8);
+    wr32(b + 8, 1);
+    wr32(b + 12, (uint32_t)h.key_kind);
+    wr32(b + 16, (uint32_t)h.gamma);
+    wr32(b + 20, (uint32_t)h.remap);
+    wr32(b + 24, (uint32_t)h.reduce);
+    wr64(b + 32, h.n); wr64(b + 40, h.P); wr64(b + 48, h.S); wr64(b + 56, h.B);
+    wr64(b + 64, h.C); wr64(b + 72, h.seed);
+    wr64(b + 80, h.remap_len); wr64(b + 88, h.remap_bytes);
+    uint64_t lb, ab;
+    memcpy(&lb, &h.lambda, 8); memcpy(&ab, &h.alpha, 8);
+    wr64(b + 96, lb); wr64(b + 104, ab);
+    wr64(b + 112, pb);
+    cudaError_t e = cudaMemcpy(b + 128, m->d_pilots, pb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h.remap_bytes)
+        e = cudaMemcpy(b + 128 + round64(pb), m->d_remap, h.remap_bytes, cudaMemcpyDeviceToHost);
+    cudaSetDevice(dev_prev);
+    if (e != cudaSuccess) return cuda_fail(e, "serialize: device to host copy");
+    return MPHF_OK;
+}
+
+static void free_handle(mphf_t *m) {
+    if (!m) return;
+    int dev_prev = 0;
+    cudaGetDevice(&dev_prev);
+    cudaSetDevice(m->device);
+    cudaFree(m->d_pilots);
+    cudaFree(m->d_remap);
+    for (int i = 0; i < 2; i++) {
+        cudaFree(m->d_stage_keys[i]);
+        cudaFree(m->d_stage_out[i]);
+        if (m->ev_h2d[i]) cudaEventDestroy(m->ev_h2d[i]);
+        if (m->ev_q[i]) cudaEventDestroy(m->ev_q[i]);
+        if (m->ev_d2h[i]) cudaEventDestroy(m->ev_d2h[i]);
+    }
+    if (m->s_h2d) cudaStreamDestroy(m->s_h2d);
+    if (m->s_d2h) cudaStreamDestroy(m->s_d2h);
+    cudaSetDevice(dev_prev);
+    delete m;
+}
+
+int mphf_deserialize(const void *host_buf, size_t len, mphf_t **out) {
+    if (!out) { set_error("out is NULL"); return MPHF_ERR_ARG; }
+    *out = nullptr;
+    if (!host_buf) { set_error("buffer is NULL"); return MPHF_ERR_ARG; }
+    const uint8_t *b = (const uint8_t *)host_buf;
+    if (len < 128 || memcmp(b, kMagic, 8) != 0 || rd32(b + 8) != 1) {
+        set_error("not a PtrHash v1 structure");
+        return MPHF_ERR_FORMAT;
+    }
+    Header h;
+    h.key_kind = (int32_t)rd32(b + 12);
+    h.gamma = (int32_t)rd32(b + 16);
+    h.remap = (int32_t)rd32(b + 20);
+    h.reduce = (int32_t)rd32(b + 24);
+    h.n = rd64(b + 32); h.P = rd64(b + 40); h.S = rd64(b + 48); h.B = rd64(b + 56);
+    h.C = rd64(b + 64); h.seed = rd64(b + 72);
+    h.remap_len = rd64(b + 80); h.remap_bytes = rd64(b + 88);
+    uint64_t lb = rd64(b + 96), ab = rd64(b + 104);
+    memcpy(&h.lambda, &lb, 8); memcpy(&h.alpha, &ab, 8);
+    const uint64_t pb = rd64(b + 112);
+    bool bad = (h.key_kind != MPHF_KEY_U64 && h.key_kind != MPHF_KEY_BYTES) ||
+               (h.gamma != MPHF_GAMMA_LINEAR && h.gamma != MPHF_GAMMA_CUBIC) ||
+               (h.remap != MPHF_REMAP_CLEF && h.remap != MPHF_REMAP_VEC) ||
+               (h.reduce != kReducePow2 && h.reduce != kReduceMod) ||
+               h.n == 0 || h.n > 0xFFFFFFFFull || h.P == 0 || h.S == 0 || h.B == 0 ||
+               h.S > 0xFFFFFFFFull || h.P > 0xFFFFFFFFull || h.B > 0xFFFFFFFFull ||
+               pb != h.P * h.B || h.P * h.S < h.n || h.P * h.S > 0xFFFFFFFFull ||
+               h.remap_len != h.P * h.S - h.n || (h.C & 1) == 0 ||
+               (h.reduce == kReducePow2 && !is_pow2(h.S)) ||
+               (h.reduce == kReduceMod && is_pow2(h.S));
+    if (!bad) {
+        uint64_t want = h.remap == MPHF_REMAP_CLEF ? 64 * clef_lines_for(h.remap_len) : 4 * h.remap_len;
+        bad = h.remap_bytes != want || len < 128 + round64(pb) + h.remap_bytes;
+    }
+    if (bad) { set_error("inconsistent header fields"); return MPHF_ERR_FORMAT; }
+    mphf_t *m = new (std::nothrow) mphf_t();
+    if (!m) { set_error("host allocation"); return MPHF_ERR_OOM; }
+    m->hdr = h;
+    cudaGetDevice(&m->device);
+    cudaError_t e = cudaMalloc(&m->d_pilots, round64(pb));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_remap, h.remap_bytes ? round64(h.remap_bytes) : 64);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_pilots, b + 128, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && h.remap_bytes)
+        e = cudaMemcpy(m->d_remap, b + 128 + round64(pb), h.remap_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "deserialize: device allocation or copy");
+        free_handle(m);
+        return rc;
+    }
+    *out = m;
+    return MPHF_OK;
+}
+
+int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
+               const uint64_t *offsets_dev, uint64_t n, void *stream, mphf_t **out) {
+    if (!out) { set_error("out is NULL"); return MPHF_ERR_ARG; }
+    *out = nullptr;
+    if (!params || !keys_dev) { set_error("NULL params or keys"); return MPHF_ERR_ARG; }
+    if (key_kind == MPHF_KEY_U64 && (offsets_dev || ((uintptr_t)keys_dev & 7))) {
+        set_error("u64 keys need 8-byte alignment and no offsets");
+        return MPHF_ERR_ARG;
+    }
+    if (key_kind == MPHF_KEY_BYTES && (!offsets_dev || ((uintptr_t)offsets_dev & 7))) {
+        set_error("byte keys need n+1 aligned u64 offsets");
+        return MPHF_ERR_ARG;
+    }
+    if (key_kind != MPHF_KEY_U64 && key_kind != MPHF_KEY_BYTES) { set_error("bad key kind"); return MPHF_ERR_ARG; }
+    BuildResult r;
+    int rc = build_structure(*params, key_kind, keys_dev, offsets_dev, n, (cudaStream_t)stream, &r);
+    if (rc) return rc;
+    mphf_t *m = new (std::nothrow) mphf_t();
+    if (!m) {
+        cudaFree(r.d_pilots);
+        cudaFree(r.d_remap);
+        set_error("host allocation");
+        return MPHF_ERR_OOM;
+    }
+    m->hdr = r.hdr;
+    m->d_pilots = r.d_pilots;
+    m->d_remap = r.d_remap;
+    m->evictions = r.evictions;
+    m->build_ms = r.build_ms;
+    cudaGetDevice(&m->device);
+    *out = m;
+    return MPHF_OK;
+}
+
+int mphf_info(const mphf_t *m, mphf_info_t *out) {
+    if (!m || !out) { set_error("NULL argument"); return MPHF_ERR_ARG; }
+    const Header &h = m->hdr;
+    memset(out, 0, sizeof(*out));
+    out->n = h.n; out->P = h.P; out->S = h.S; out->B = h.B; out->C = h.C; out->seed = h.seed;
+    out->gamma = h.gamma; out->remap = h.remap; out->reduce = h.reduce; out->key_kind = h.key_kind;
+    out->remap_len = h.remap_len;
+    out->pilot_bytes = h.P * h.B;
+    out->remap_bytes = h.remap_bytes;
+    out->bits_per_key = 8.0 * (double)(out->pilot_bytes + out->remap_bytes) / (double)h.n;
+    out->evictions = m->evictions;
+    out->build_ms = m->build_ms;
+    return MPHF_OK;
+}
+
+void mphf_free(mphf_t *m) { free_handle(m); }
+
+int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
+                   void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    if (!keys_dev || !out_dev || ((uintptr_t)keys_dev & 7) || ((uintptr_t)out_dev & 3)) {
+        set_error("keys must be 8-byte and out 4-byte aligned device pointers");
+        return MPHF_ERR_ARG;
+    }
+    if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, false, (cudaStream_t)stream);
+}
+
+int mphf_query_u64_phf(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
+                       void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    if (!keys_dev || !out_dev || ((uintptr_t)keys_dev & 7) || ((uintptr_t)out_dev & 3)) {
+        set_error("keys must be 8-byte and out 4-byte aligned device pointers");
+        return MPHF_ERR_ARG;
+    }
+    if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, true, (cudaStream_t)stream);
+}
+
+int mphf_query_bytes(const mphf_t *m, const uint8_t *bytes_dev, const uint64_t *offsets_dev,
+                     uint64_t count, uint32_t *out_dev, void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    if (!bytes_dev || !offsets_dev || !out_dev || ((uintptr_t)offsets_dev & 7) || ((uintptr_t)out_dev & 3)) {
+        set_error("bad pointers for byte-key query");
+        return MPHF_ERR_ARG;
+    }
+    if (m->hdr.key_kind != MPHF_KEY_BYTES) { set_error("structure was built for u64 keys"); return MPHF_ERR_ARG; }
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    return launch_query_bytes(m->hdr, v, bytes_dev, offsets_dev, count, out_dev, (cudaStream_t)stream);
+}
+
+// Host-buffer query: chunk c uses buffer set c % 2.  The copy in of chunk c
+// waits for the kernel of chunk c-2 (same key buffer); the kernel of chunk c
+// waits for its copy in and for the copy out of chunk c-2 (same output
+// buffer); the copy out of chunk c waits for its kernel.  So copy-in,
+// kernel and copy-out of consecutive chunks overlap.
+int mphf_query_u64_host(mphf_t *m, const uint64_t *keys_host, uint64_t count, uint32_t *out_host,
+                        void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    if (!keys_host || !out_host) { set_error("NULL host buffer"); return MPHF_ERR_ARG; }
+    if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(m->stage_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t chunk = 1ull << 24;
+    cudaError_t e = cudaSuccess;
+    if (m->stage_chunk == 0) {
+        for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+            e = cudaMalloc(&m->d_stage_keys[i], chunk * sizeof(uint64_t));
+            if (e == cudaSuccess) e = cudaMalloc(&m->d_stage_out[i], chunk * sizeof(uint32_t));
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_h2d[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_q[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_d2h[i], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->s_h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->s_d2h, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "host query: staging setup");
+        m->stage_chunk = chunk;
+    }
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    // Order the first copies after earlier work on the caller's stream.
+    e = cudaEventRecord(m->ev_q[0], s);
+    if (e == cudaSuccess) e = cudaEventRecord(m->ev_q[1], s);
+    if (e == cudaSuccess) e = cudaEventRecord(m->ev_d2h[0], s);
+    if (e == cudaSuccess) e = cudaEventRecord(m->ev_d2h[1], s);
+    int rc = MPHF_OK;
+    for (uint64_t off = 0, c = 0; off < count && e == cudaSuccess && rc == MPHF_OK; off += chunk, c++) {
+        const int b = (int)(c & 1);
+        const uint64_t cnt = count - off < chunk ? count - off : chunk;
+        e = cudaStreamWaitEvent(m->s_h2d, m->ev_q[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_stage_keys[b], keys_host + off, cnt * 8, cudaMemcpyHostToDevice, m->s_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(m->ev_h2d[b], m->s_h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev_h2d[b], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev_d2h[b], 0);
+        if (e != cudaSuccess) break;
+        rc = launch_query_u64(m->hdr, v, m->d_stage_keys[b], cnt, m->d_stage_out[b], false, s);
+        if (rc) break;
+        e = cudaEventRecord(m->ev_q[b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->s_d2h, m->ev_q[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_host + off, m->d_stage_out[b], cnt * 4, cudaMemcpyDeviceToHost, m->s_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(m->ev_d2h[b], m->s_d2h);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(m->s_d2h);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "host query: copy pipeline");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "host query: copy-out stream");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "host query: compute stream");
+    return MPHF_OK;
+}
+
+const char *mphf_strerror(int code) {
+    switch (code) {
+        case MPHF_OK: return "ok";
+        case MPHF_ERR_ARG: return "invalid argument";
+        case MPHF_ERR_OOM: return "out of memory";
+        case MPHF_ERR_DUP_KEYS: return "duplicate keys";
+        case MPHF_ERR_BUILD_FAILED: return "construction failed after every reseed";
+        case MPHF_ERR_FORMAT: return "invalid serialized structure";
+        case MPHF_ERR_CUDA: return "CUDA error";
+        case MPHF_ERR_TIMEOUT: return "device wait timed out";
+        case MPHF_ERR_OVERFULL: return "a part holds more keys than slots";
+        case MPHF_ERR_CAPACITY: return "capacity exceeded";
+        default: return "unknown error";
+    }
+}
+
+const char *mphf_last_error(void) { return g_err; }
+
+uint64_t mphf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,694 @@
+// GPU construction of a PtrHash structure (Sec. 3.2 and Sec. 3.4).
+//
+//   1. hash every key                                   (hash_keys_kernel)
+//   2. radix-sort the 64-bit hashes (CUB); sorted hashes are grouped by part
+//      and, inside a part, by bucket, because part = hi(P h) and the bucket
+//      function are monotone in h
+//   3. bucket boundaries, duplicate and part-size checks  (bucket_bounds_kernel)
+//   4. pilot search, one CTA per part, the part's taken-slot bitvector in
+//      shared memory: buckets in order of decreasing size, the smallest pilot
+//      whose keys land on distinct free slots; else the pilot of least
+//      weighted collisions (weight s^2 for a key of a bucket of size s),
+//      evicting the colliding buckets, never one of the 16 most recently
+//      placed; a part fails after evict_mult * S evictions  (pilot_search_kernel)
+//   5. remap: the R taken slots >= n in order go to the R free slots < n in
+//      order, F[q - n]; other entries repeat their predecessor; CacheLineEF
+//      encoding of F, or a plain u32 array if a line's span does not fit.
+// A failed part or equal string hashes restart from step 1 with seed + 1.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <vector>
+
+#include "mphf_internal.cuh"
+
+namespace ptrhash {
+
+constexpr int kSearchThreads = 256;
+constexpr int kMaxBucket = 2048;        // larger buckets fail the part
+constexpr int kSmallBucket = 16;        // pilot-parallel search up to this size
+constexpr int kPendingCap = 4096;       // evicted buckets waiting for a pilot
+constexpr int kSetSize = 4096;          // slot set for self-collision checks
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint64_t kMaxSlots = 1ull << 20;   // bitvector in shared memory
+
+enum : uint32_t { kPartOk = 0, kPartNoPilot = 1, kPartEvictCap = 2, kPartBigBucket = 3, kPartPendingFull = 4 };
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+// ---------------------------------------------------------- step 3: bounds
+template <int GAMMA>
+__device__ __forceinline__ uint64_t global_bucket(uint64_t h, uint64_t P, uint64_t B) {
+    const uint64_t part = mul_hi(P, h);
+    return part * B + mul_hi(B, bucket_fn<GAMMA>(P * h));
+}
+
+// bstart[b] = index of the first sorted hash in global bucket b (b <= P*B).
+template <int GAMMA>
+__global__ void bucket_bounds_kernel(const uint64_t *__restrict__ sorted, uint64_t n, uint64_t P, uint64_t B,
+                                     uint32_t *__restrict__ bstart, uint32_t *__restrict__ dup) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t hi_b = i < n ? global_bucket<GAMMA>(sorted[i], P, B) : P * B;
+        const uint64_t lo_b = i > 0 ? global_bucket<GAMMA>(sorted[i - 1], P, B) + 1 : 0;
+        for (uint64_t b = lo_b; b <= hi_b; b++) bstart[b] = (uint32_t)i;
+        if (i > 0 && i < n && sorted[i] == sorted[i - 1]) *dup = 1;
+    }
+}
+
+__global__ void part_size_kernel(const uint32_t *__restrict__ bstart, uint64_t P, uint64_t B, uint64_t S,
+                                 uint32_t *__restrict__ overfull) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x)
+        if (bstart[(p + 1) * B] - bstart[p * B] > S) *overfull = 1;
+}
+
+// ------------------------------------------------------ step 4: the search
+struct SearchArgs {
+    const uint64_t *sorted;
+    const uint32_t *bstart;
+    uint8_t *pilots;
+    uint32_t *taken;          // linear bitmap of P*S bits (zeroed)
+    uint32_t *owner_scratch;  // gridDim.x * S
+    uint32_t *order_scratch;  // gridDim.x * B
+    uint32_t *status;         // per part
+    unsigned long long *evictions;
+    uint32_t *next_part;
+    uint64_t P, S, B, C, seed, fm_hi, fm_lo, s_mask, evict_cap;
+};
+
+template <int REDUCE>
+__device__ __forceinline__ uint32_t slot_in_part(const SearchArgs &a, uint64_t x) {
+    if constexpr (REDUCE == kReducePow2) return (uint32_t)(mul_hi(a.C, x) & a.s_mask);
+    else return (uint32_t)mod_direct(x, a.fm_hi, a.fm_lo, a.S);
+}
+
+__device__ __forceinline__ bool bit_of(const uint32_t *bits, uint32_t s) { return (bits[s >> 5] >> (s & 31)) & 1u; }
+
+struct SearchShared {
+    uint32_t *bits;     // S bits
+    uint32_t *hist;     // kMaxBucket + 1
+    uint64_t *hcache;   // kMaxBucket hashes of the current bucket
+    uint32_t *set;      // kSetSize slot-set entries (generation << 21 | slot)
+    uint32_t *pending;  // kPendingCap
+    uint32_t *recent;   // 16
+};
+
+// Inserts slot s for generation gen; false if it is already in the set.
+__device__ __forceinline__ bool set_insert(uint32_t *set, uint32_t s, uint32_t gen) {
+    const uint32_t key = (gen << 21) | s;
+    uint32_t idx = (s * 2654435761u) & (kSetSize - 1);
+    for (int probe = 0; probe < kSetSize; probe++) {
+        uint32_t e = set[idx];
+        while ((e >> 21) != gen) {               // stale entry of an older generation: free
+            const uint32_t prev = atomicCAS(&set[idx], e, key);
+            if (prev == e) return true;
+            e = prev;
+        }
+        if ((e & 0x1FFFFFu) == s) return false;
+        idx = (idx + 1) & (kSetSize - 1);
+    }
+    return false;                                 // cannot happen: load <= 1/2
+}
+
+__device__ __forceinline__ uint32_t bump_gen(uint32_t gen, uint32_t *set, int lane) {
+    if (++gen < 2048) return gen;
+    for (int i = lane; i < kSetSize; i += 32) set[i] = 0;
+    __syncwarp();
+    return 1;
+}
+
+__device__ __forceinline__ bool in_recent(const uint32_t *recent, uint32_t b) {
+    bool r = false;
+#pragma unroll
+    for (int i = 0; i < 16; i++) r |= recent[i] == b;
+    return r;
+}
+
+// Pilot-parallel greedy search for a bucket of s <= kSmallBucket keys: lane
+// l tries pilot 32 r + l in round r; the smallest successful pilot wins.
+// myh is key `lane`'s hash (lanes >= s hold anything).
+template <int REDUCE>
+__device__ int greedy_small(const SearchArgs &a, const uint32_t *bits, uint64_t myh, int s, int lane) {
+    for (int r = 0; r < 8; r++) {
+        const uint64_t hp = a.C * ((uint64_t)(32 * r + lane) ^ a.seed);
+        uint32_t sl[kSmallBucket];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < kSmallBucket; j++) {
+            const uint64_t hj = __shfl_sync(0xFFFFFFFFu, myh, j);
+            if (j < s) {
+                sl[j] = slot_in_part<REDUCE>(a, hj ^ hp);
+                ok &= !bit_of(bits, sl[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 1; j < kSmallBucket; j++)
+#pragma unroll
+            for (int k = 0; k < j; k++)
+                if (j < s && sl[j] == sl[k]) ok = false;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+        if (m) return 32 * r + __ffs(m) - 1;
+    }
+    return -1;
+}
+
+// Key-parallel greedy search for a large bucket: pilots in increasing order,
+// lanes over the keys, self-collisions found through the slot set.
+template <int REDUCE>
+__device__ int greedy_large(const SearchArgs &a, const SearchShared &sh, int s, uint32_t &gen, int lane) {
+    for (int p = 0; p < 256; p++) {
+        const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
+        gen = bump_gen(gen, sh.set, lane);
+        bool bad = false;
+        for (int j = lane; j < s; j += 32) {
+            const uint32_t sl = slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp);
+            if (bit_of(sh.bits, sl) || !set_insert(sh.set, sl, gen)) bad = true;
+        }
+        if (!__any_sync(0xFFFFFFFFu, bad)) return p;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ uint64_t bucket_size(const SearchArgs &a, uint64_t gb0, uint32_t b) {
+    return a.bstart[gb0 + b + 1] - a.bstart[gb0 + b];
+}
+
+// Least weighted collisions (Sec. 3.2): cost = sum over the bucket's keys
+// that hit a taken slot of size(owner)^2; pilots that self-collide or hit
+// one of the 16 most recently placed buckets are not allowed.  Ties go to
+// the smaller pilot.  Returns -1 if no pilot is allowed.
+template <int REDUCE>
+__device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const uint32_t *owner, uint64_t gb0,
+                            uint64_t myh, int s, uint32_t &gen, int lane) {
+    uint64_t best_cost = ~0ull;
+    int best_p = -1;
+    if (s <= kSmallBucket) {
+        for (int r = 0; r < 8; r++) {
+            const int p = 32 * r + lane;
+            const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
+            uint32_t sl[kSmallBucket];
+            bool ok = true;
+            uint64_t cost = 0;
+#pragma unroll
+            for (int j = 0; j < kSmallBucket; j++) {
+                const uint64_t hj = __shfl_sync(0xFFFFFFFFu, myh, j);
+                if (j < s) {
+                    sl[j] = slot_in_part<REDUCE>(a, hj ^ hp);
+                    if (bit_of(sh.bits, sl[j])) {
+                        const uint32_t o = owner[sl[j]];
+                        if (in_recent(sh.recent, o)) ok = false;
+                        const uint64_t z = bucket_size(a, gb0, o);
+                        cost += z * z;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 1; j < kSmallBucket; j++)
+#pragma unroll
+                for (int k = 0; k < j; k++)
+                    if (j < s && sl[j] == sl[k]) ok = false;
+            uint64_t c = ok ? cost : ~0ull;
+            int pp = ok ? p : 0x7FFFFFFF;
+            for (int off = 16; off; off >>= 1) {
+                const uint64_t oc = __shfl_xor_sync(0xFFFFFFFFu, c, off);
+                const int op = __shfl_xor_sync(0xFFFFFFFFu, pp, off);
+                if (oc < c || (oc == c && op < pp)) { c = oc; pp = op; }
+            }
+            if (c < best_cost) { best_cost = c; best_p = pp; }
+        }
+        return best_p;
+    }
+    for (int p = 0; p < 256; p++) {
+        const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
+        gen = bump_gen(gen, sh.set, lane);
+        bool bad = false;
+        uint64_t cost = 0;
+        for (int j = lane; j < s; j += 32) {
+            const uint32_t sl = slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp);
+            if (!set_insert(sh.set, sl, gen)) bad = true;
+            else if (bit_of(sh.bits, sl)) {
+                const uint32_t o = owner[sl];
+                if (in_recent(sh.recent, o)) bad = true;
+                const uint64_t z = bucket_size(a, gb0, o);
+                cost += z * z;
+            }
+        }
+        bad = __any_sync(0xFFFFFFFFu, bad);
+        for (int off = 16; off; off >>= 1) cost += __shfl_xor_sync(0xFFFFFFFFu, cost, off);
+        if (!bad && cost < best_cost) { best_cost = cost; best_p = p; }
+    }
+    return best_p;
+}
+
+// Greedy + hash-evict placement of one part by one warp.  Returns a status.
+template <int REDUCE>
+__device__ uint32_t search_part(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint32_t *order,
+                                uint32_t nb, uint64_t p, int lane, unsigned long long &evicted) {
+    const uint64_t gb0 = p * a.B;
+    uint32_t next = 0, np = 0, rpos = 0, gen = 0;
+    for (int i = lane; i < 16; i += 32) sh.recent[i] = kNone;
+    for (int i = lane; i < kSetSize; i += 32) sh.set[i] = 0;
+    __syncwarp();
+    for (;;) {
+        // The largest waiting bucket: next in the size order, or an evicted one.
+        uint64_t best_sz = 0;
+        uint32_t best_i = kNone;
+        for (uint32_t i = lane; i < np; i += 32) {
+            const uint64_t z = bucket_size(a, gb0, sh.pending[i]);
+            if (z > best_sz || (z == best_sz && i < best_i)) { best_sz = z; best_i = i; }
+        }
+        for (int off = 16; off; off >>= 1) {
+            const uint64_t oz = __shfl_xor_sync(0xFFFFFFFFu, best_sz, off);
+            const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, best_i, off);
+            if (oz > best_sz || (oz == best_sz && oi < best_i)) { best_sz = oz; best_i = oi; }
+        }
+        const uint32_t ord_b = next < nb ? order[next] : kNone;
+        const uint64_t ord_sz = ord_b != kNone ? bucket_size(a, gb0, ord_b) : 0;
+        if (ord_b == kNone && np == 0) return kPartOk;
+        uint32_t b;
+        if (np > 0 && best_sz >= ord_sz) {   // ties: the evicted bucket goes first
+            b = sh.pending[best_i];
+            __syncwarp();
+            if (lane == 0) sh.pending[best_i] = sh.pending[np - 1];
+            np--;
+            __syncwarp();
+        } else {
+            b = ord_b;
+            next++;
+        }
+        const int s = (int)bucket_size(a, gb0, b);
+        const uint64_t kbase = a.bstart[gb0 + b];
+        uint64_t myh = lane < s ? a.sorted[kbase + lane] : 0;
+        if (s > kSmallBucket) {
+            for (int j = lane; j < s; j += 32) sh.hcache[j] = a.sorted[kbase + j];
+            __syncwarp();
+        }
+        int chosen = s <= kSmallBucket ? greedy_small<REDUCE>(a, sh.bits, myh, s, lane)
+                                       : greedy_large<REDUCE>(a, sh, s, gen, lane);
+        if (chosen < 0) {
+            chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane);
+            if (chosen < 0) return kPartNoPilot;
+            const uint64_t hp = a.C * ((uint64_t)chosen ^ a.seed);
+            for (int j = 0; j < s; j++) {
+                const uint64_t hj = s <= kSmallBucket ? __shfl_sync(0xFFFFFFFFu, myh, j) : sh.hcache[j];
+                const uint32_t sl = slot_in_part<REDUCE>(a, hj ^ hp);
+                if (!bit_of(sh.bits, sl)) continue;        // free, or its owner already evicted
+                const uint32_t o = owner[sl];
+                const uint64_t ob = a.bstart[gb0 + o];
+                const uint64_t os = bucket_size(a, gb0, o);
+                const uint64_t ohp = a.C * ((uint64_t)a.pilots[gb0 + o] ^ a.seed);
+                for (uint64_t k = lane; k < os; k += 32) {
+                    const uint32_t osl = slot_in_part<REDUCE>(a, a.sorted[ob + k] ^ ohp);
+                    atomicAnd(&sh.bits[osl >> 5], ~(1u << (osl & 31)));
+                }
+                if (np >= (uint32_t)kPendingCap) return kPartPendingFull;
+                if (lane == 0) sh.pending[np] = o;
+                np++;
+                evicted++;
+                __syncwarp();
+            }
+            if (evicted > a.evict_cap) return kPartEvictCap;
+        }
+        const uint64_t hp = a.C * ((uint64_t)chosen ^ a.seed);
+        for (int j = lane; j < s; j += 32) {
+            const uint64_t hj = s <= kSmallBucket ? myh : sh.hcache[j];
+            const uint32_t sl = slot_in_part<REDUCE>(a, hj ^ hp);
+            atomicOr(&sh.bits[sl >> 5], 1u << (sl & 31));
+            owner[sl] = b;
+        }
+        if (lane == 0) {
+            a.pilots[gb0 + b] = (uint8_t)chosen;
+            sh.recent[rpos] = b;
+        }
+        rpos = (rpos + 1) & 15;
+        __syncwarp();
+    }
+}
+
+template <int REDUCE>
+__global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint64_t words = (a.S + 31) / 32;
+    SearchShared sh;
+    sh.hcache = reinterpret_cast<uint64_t *>(smem);
+    sh.bits = reinterpret_cast<uint32_t *>(sh.hcache + kMaxBucket);
+    sh.hist = sh.bits + words;
+    sh.set = sh.hist + (kMaxBucket + 1);
+    sh.pending = sh.set + kSetSize;
+    sh.recent = sh.pending + kPendingCap;
+    __shared__ uint32_t s_part, s_flag, s_nb, s_status;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *owner = a.owner_scratch + (uint64_t)blockIdx.x * a.S;
+    uint32_t *order = a.order_scratch + (uint64_t)blockIdx.x * a.B;
+    for (;;) {
+        if (tid == 0) { s_part = atomicAdd(a.next_part, 1u); s_flag = 0; }
+        __syncthreads();
+        const uint64_t p = s_part;
+        if (p >= a.P) break;
+        const uint64_t gb0 = p * a.B;
+        for (uint64_t w = tid; w < words; w += blockDim.x) sh.bits[w] = 0;
+        for (int z = tid; z <= kMaxBucket; z += blockDim.x) sh.hist[z] = 0;
+        __syncthreads();
+        for (uint64_t b = tid; b < a.B; b += blockDim.x) {
+            const uint32_t z = a.bstart[gb0 + b + 1] - a.bstart[gb0 + b];
+            if (z > (uint32_t)kMaxBucket) s_flag = 1;
+            else if (z) atomicAdd(&sh.hist[z], 1u);
+        }
+        __syncthreads();
+        if (s_flag) {
+            if (tid == 0) a.status[p] = kPartBigBucket;
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0) {   // exclusive offsets in order of decreasing size
+            uint32_t run = 0;
+            for (int z = kMaxBucket; z >= 1; z--) { const uint32_t c = sh.hist[z]; sh.hist[z] = run; run += c; }
+            s_nb = run;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // Stable scatter: same-size buckets keep increasing bucket order.
+            for (uint64_t base = 0; base < a.B; base += 32) {
+                const uint64_t b = base + lane;
+                const uint32_t z = b < a.B ? a.bstart[gb0 + b + 1] - a.bstart[gb0 + b] : 0;
+                const unsigned peers = __match_any_sync(0xFFFFFFFFu, z);
+                const unsigned rank = __popc(peers & ((1u << lane) - 1));
+                uint32_t pos = 0;
+                if (z) pos = sh.hist[z] + rank;
+                __syncwarp();
+                if (z) {
+                    order[pos] = (uint32_t)b;
+                    if (rank == 0) sh.hist[z] += __popc(peers);
+                }
+                __syncwarp();
+            }
+            unsigned long long ev = 0;
+            const uint32_t st = search_part<REDUCE>(a, sh, owner, order, s_nb, p, lane, ev);
+            if (lane == 0) {
+                a.status[p] = st;
+                atomicAdd(a.evictions, ev);
+                s_status = st;
+            }
+        }
+        __syncthreads();
+        if (s_status == kPartOk) {   // publish the part's slots into the global bitmap
+            for (uint64_t w = tid; w < words; w += blockDim.x) {
+                const uint32_t word = sh.bits[w];
+                if (!word) continue;
+                const uint64_t g = p * a.S + 32 * w;
+                const uint32_t sh_ = (uint32_t)(g & 31);
+                atomicOr(&a.taken[g >> 5], word << sh_);
+                if (sh_) atomicOr(&a.taken[(g >> 5) + 1], word >> (32 - sh_));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ step 5: remap
+// Word w of the bitmap covers slots [32 w, 32 w + 32).
+__device__ __forceinline__ uint32_t low_mask(uint64_t w, uint64_t n) {   // bits of slots < n
+    const uint64_t a = 32 * w;
+    if (a + 32 <= n) return 0xFFFFFFFFu;
+    if (a >= n) return 0;
+    return (1u << (n - a)) - 1;
+}
+__device__ __forceinline__ uint32_t range_mask(uint64_t w, uint64_t lo, uint64_t hi) {  // slots in [lo, hi)
+    const uint64_t a = 32 * w;
+    uint32_t m = 0xFFFFFFFFu;
+    if (lo > a) m &= lo - a >= 32 ? 0 : ~((1u << (lo - a)) - 1);
+    if (hi < a + 32) m &= hi <= a ? 0 : (1u << (hi - a)) - 1;
+    return m;
+}
+
+__global__ void remap_count_kernel(const uint32_t *__restrict__ taken, uint64_t words, uint64_t n, uint64_t total,
+                                   uint32_t *__restrict__ free_cnt, uint32_t *__restrict__ high_cnt) {
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = taken[w];
+        free_cnt[w] = __popc(~t & low_mask(w, n));
+        high_cnt[w] = __popc(t & range_mask(w, n, total));
+    }
+}
+
+// L[r] = position of the r-th free slot below n.
+__global__ void free_list_kernel(const uint32_t *__restrict__ taken, uint64_t words, uint64_t n,
+                                 const uint32_t *__restrict__ free_rank, uint32_t *__restrict__ L) {
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t m = ~taken[w] & low_mask(w, n);
+        uint32_t r = free_rank[w];
+        while (m) {
+            const int bpos = __ffs(m) - 1;
+            L[r++] = (uint32_t)(32 * w + bpos);
+            m &= m - 1;
+        }
+    }
+}
+
+// F[j] = L[t - 1] with t the number of taken slots in [n, n + j]; entries
+// before the first taken slot take L[0]; all zero when R = 0.
+__global__ void remap_values_kernel(const uint32_t *__restrict__ taken, const uint32_t *__restrict__ high_rank,
+                                    const uint32_t *__restrict__ L, uint64_t n, uint64_t total, uint64_t R,
+                                    uint32_t *__restrict__ F) {
+    const uint64_t len = total - n;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = n + j, w = q >> 5;
+        const uint32_t upto = (q & 31) == 31 ? 0xFFFFFFFFu : (2u << (q & 31)) - 1;
+        const uint64_t t = high_rank[w] + __popc(taken[w] & range_mask(w, n, total) & upto);
+        F[j] = R ? L[t ? t - 1 : 0] : 0;
+    }
+}
+
+// One CacheLineEF line per thread (Sec. 3.4, Eq. clef).
+__global__ void clef_encode_kernel(const uint32_t *__restrict__ F, uint64_t len, uint64_t lines,
+                                   uint8_t *__restrict__ out, uint32_t *__restrict__ span_fail) {
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < lines; c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i0 = c * kClefPerLine;
+        const uint32_t v0 = F[i0];
+        const uint32_t offset = v0 >> 8;
+        uint32_t words[4] = {0, 0, 0, 0};
+        uint8_t *line = out + 64 * c;
+        for (int i = 0; i < kClefPerLine; i++) {
+            const uint64_t idx = i0 + i < len ? i0 + i : len - 1;
+            const uint32_t v = F[idx];
+            const uint32_t bit = i + ((v >> 8) - offset);
+            if (bit >= 128) { *span_fail = 1; break; }
+            words[bit >> 5] |= 1u << (bit & 31);
+            line[20 + i] = (uint8_t)v;
+        }
+        reinterpret_cast<uint4 *>(line)[0] = make_uint4(words[0], words[1], words[2], words[3]);
+        reinterpret_cast<uint32_t *>(line)[4] = offset;
+    }
+}
+
+// ------------------------------------------------------------ orchestration
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+    void *release() { void *q = p; p = nullptr; return q; }
+};
+
+static unsigned grid_for(uint64_t work, int sms) {
+    const uint64_t want = (work + 255) / 256;
+    const uint64_t cap = (uint64_t)sms * 32;
+    return (unsigned)(want == 0 ? 1 : (want < cap ? want : cap));
+}
+
+template <int REDUCE>
+static cudaError_t launch_search(const SearchArgs &a, unsigned grid, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(pilot_search_kernel<REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    pilot_search_kernel<REDUCE><<<grid, kSearchThreads, smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int build_structure(const mphf_params &prm, int key_kind, const void *keys, const uint64_t *offsets, uint64_t n,
+                    cudaStream_t s, BuildResult *out) {
+    if (!(prm.C & 1)) { set_error("mixing constant C must be odd"); return MPHF_ERR_ARG; }
+    if (prm.gamma != MPHF_GAMMA_LINEAR && prm.gamma != MPHF_GAMMA_CUBIC) { set_error("bad gamma"); return MPHF_ERR_ARG; }
+    if (prm.remap != MPHF_REMAP_CLEF && prm.remap != MPHF_REMAP_VEC) { set_error("bad remap kind"); return MPHF_ERR_ARG; }
+    uint64_t P, S, B;
+    int reduce;
+    int rc = choose_layout(n, prm.lambda, prm.alpha, prm.slots_override, &P, &S, &B, &reduce);
+    if (rc) return rc;
+    if (S > kMaxSlots) { set_error("S=%llu above the %llu slots a part can hold", (unsigned long long)S, (unsigned long long)kMaxSlots); return MPHF_ERR_CAPACITY; }
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+    cudaEvent_t t0, t1;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    CK(cudaEventRecord(t0, s));
+
+    const uint64_t total = P * S, nbkt = P * B, words = (total + 31) / 32;
+    const unsigned search_grid = (unsigned)(P < (uint64_t)sms ? P : (uint64_t)sms);
+    DevBuf hash, sorted, bstart, pilots, taken, owner, order, status, flags, cub_tmp;
+    CK(hash.alloc(n * 8));
+    CK(sorted.alloc(n * 8));
+    CK(bstart.alloc((nbkt + 1) * 4));
+    CK(pilots.alloc((nbkt + 63) & ~63ull));
+    CK(taken.alloc((words + 1) * 4));
+    CK(owner.alloc((uint64_t)search_grid * S * 4));
+    CK(order.alloc((uint64_t)search_grid * B * 4));
+    CK(status.alloc(P * 4));
+    CK(flags.alloc(64));
+    size_t sort_tmp = 0;
+    CK(cub::DeviceRadixSort::SortKeys(nullptr, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), n, 0, 64, s));
+    CK(cub_tmp.alloc(sort_tmp));
+    uint32_t *d_flags = flags.as<uint32_t>();   // [0] dup, [1] overfull, [2] next part, [3] span, [4..5] evictions
+
+    const size_t smem = kMaxBucket * 8 + ((S + 31) / 32) * 4 + (kMaxBucket + 1) * 4 + kSetSize * 4 + kPendingCap * 4 + 16 * 4;
+    Header h;
+    h.n = n; h.P = P; h.S = S; h.B = B; h.C = prm.C; h.gamma = prm.gamma; h.reduce = reduce;
+    h.key_kind = key_kind; h.lambda = prm.lambda; h.alpha = prm.alpha; h.remap_len = total - n;
+    uint64_t evictions_total = 0;
+    bool built = false;
+    int last_fail = MPHF_ERR_BUILD_FAILED;
+    const int attempts = prm.max_reseeds < 0 ? 1 : prm.max_reseeds + 1;
+    for (int attempt = 0; attempt < attempts && !built; attempt++) {
+        const uint64_t seed = prm.seed + (uint64_t)attempt;
+        h.seed = seed;
+        CK(cudaMemsetAsync(d_flags, 0, 64, s));
+        rc = launch_hash_keys(key_kind, keys, offsets, n, prm.C, seed, hash.as<uint64_t>(), sms, s);
+        if (rc) return rc;
+        CK(cub::DeviceRadixSort::SortKeys(cub_tmp.p, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), n, 0, 64, s));
+        count_launch(4);
+        if (prm.gamma == MPHF_GAMMA_CUBIC)
+            bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted.as<uint64_t>(), n, P, B, bstart.as<uint32_t>(), d_flags);
+        else
+            bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted.as<uint64_t>(), n, P, B, bstart.as<uint32_t>(), d_flags);
+        part_size_kernel<<<grid_for(P, sms), 256, 0, s>>>(bstart.as<uint32_t>(), P, B, S, d_flags + 1);
+        count_launch(2);
+        CK(cudaGetLastError());
+        uint32_t hf[2];
+        CK(cudaMemcpyAsync(hf, d_flags, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hf[0]) {
+            last_fail = MPHF_ERR_DUP_KEYS;
+            set_error("equal key hashes (duplicate keys)");
+            if (key_kind == MPHF_KEY_U64) return MPHF_ERR_DUP_KEYS;   // h = C k: duplicates for sure
+            continue;
+        }
+        if (hf[1]) {
+            last_fail = MPHF_ERR_OVERFULL;
+            set_error("a part holds more than S=%llu keys", (unsigned long long)S);
+            if (key_kind == MPHF_KEY_U64) return MPHF_ERR_OVERFULL;   // the seed does not move u64 keys
+            continue;
+        }
+        CK(cudaMemsetAsync(taken.p, 0, (words + 1) * 4, s));
+        CK(cudaMemsetAsync(pilots.p, 0, nbkt, s));
+        SearchArgs a;
+        a.sorted = sorted.as<uint64_t>(); a.bstart = bstart.as<uint32_t>(); a.pilots = pilots.as<uint8_t>();
+        a.taken = taken.as<uint32_t>(); a.owner_scratch = owner.as<uint32_t>(); a.order_scratch = order.as<uint32_t>();
+        a.status = status.as<uint32_t>();
+        a.evictions = reinterpret_cast<unsigned long long *>(d_flags + 4);
+        a.next_part = d_flags + 2;
+        a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;
+        a.fm_hi = a.fm_lo = 0;
+        if (reduce == kReduceMod) fastmod_constant(S, &a.fm_hi, &a.fm_lo);
+        a.evict_cap = (uint64_t)prm.evict_mult * S;
+        CK(reduce == kReducePow2 ? launch_search<kReducePow2>(a, search_grid, smem, s)
+                                 : launch_search<kReduceMod>(a, search_grid, smem, s));
+        std::vector<uint32_t> st(P);
+        unsigned long long ev = 0;
+        CK(cudaMemcpyAsync(st.data(), status.p, P * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&ev, d_flags + 4, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        evictions_total += ev;
+        uint64_t failed = 0, first_bad = 0;
+        for (uint64_t p = 0; p < P; p++) if (st[p] != kPartOk) { if (!failed) first_bad = p; failed++; }
+        if (failed) {
+            last_fail = MPHF_ERR_BUILD_FAILED;
+            set_error("%llu part(s) failed (first: part %llu, status %u) with seed %llu", (unsigned long long)failed,
+                      (unsigned long long)first_bad, st[first_bad], (unsigned long long)seed);
+            continue;
+        }
+        built = true;
+    }
+    if (!built) return last_fail;
+
+    // Remap (Sec. 3.4).
+    const uint64_t len = total - n;
+    DevBuf free_cnt, high_cnt, free_rank, high_rank, L, F, remap;
+    CK(free_cnt.alloc(words * 4));
+    CK(high_cnt.alloc(words * 4));
+    CK(free_rank.alloc((words + 1) * 4));
+    CK(high_rank.alloc((words + 1) * 4));
+    remap_count_kernel<<<grid_for(words, sms), 256, 0, s>>>(taken.as<uint32_t>(), words, n, total,
+                                                            free_cnt.as<uint32_t>(), high_cnt.as<uint32_t>());
+    count_launch();
+    size_t scan_tmp = 0;
+    CK(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, free_cnt.as<uint32_t>(), free_rank.as<uint32_t>(), words, s));
+    DevBuf scan_buf;
+    CK(scan_buf.alloc(scan_tmp));
+    CK(cub::DeviceScan::ExclusiveSum(scan_buf.p, scan_tmp, free_cnt.as<uint32_t>(), free_rank.as<uint32_t>(), words, s));
+    CK(cub::DeviceScan::ExclusiveSum(scan_buf.p, scan_tmp, high_cnt.as<uint32_t>(), high_rank.as<uint32_t>(), words, s));
+    count_launch(2);
+    uint32_t tail[4];
+    CK(cudaMemcpyAsync(&tail[0], free_rank.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tail[1], free_cnt.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tail[2], high_rank.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tail[3], high_cnt.as<uint32_t>() + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t R_low = (uint64_t)tail[0] + tail[1], R_high = (uint64_t)tail[2] + tail[3];
+    if (R_low != R_high) {
+        set_error("internal: %llu free slots below n but %llu keys at or above n", (unsigned long long)R_low,
+                  (unsigned long long)R_high);
+        return MPHF_ERR_BUILD_FAILED;
+    }
+    CK(L.alloc(R_low * 4));
+    CK(F.alloc(len * 4));
+    free_list_kernel<<<grid_for(words, sms), 256, 0, s>>>(taken.as<uint32_t>(), words, n, free_rank.as<uint32_t>(), L.as<uint32_t>());
+    remap_values_kernel<<<grid_for(len, sms), 256, 0, s>>>(taken.as<uint32_t>(), high_rank.as<uint32_t>(), L.as<uint32_t>(),
+                                                           n, total, R_low, F.as<uint32_t>());
+    count_launch(2);
+    int remap_kind = prm.remap;
+    if (remap_kind == MPHF_REMAP_CLEF && len > 0) {
+        const uint64_t lines = clef_lines_for(len);
+        CK(remap.alloc(lines * 64));
+        clef_encode_kernel<<<grid_for(lines, sms), 256, 0, s>>>(F.as<uint32_t>(), len, lines, remap.as<uint8_t>(), d_flags + 3);
+        count_launch();
+        uint32_t span_fail = 0;
+        CK(cudaMemcpyAsync(&span_fail, d_flags + 3, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (span_fail) {               // a line's values span too far: plain array instead
+            cudaFree(remap.release());
+            remap_kind = MPHF_REMAP_VEC;
+        } else {
+            h.remap_bytes = lines * 64;
+        }
+    } else if (remap_kind == MPHF_REMAP_CLEF) {
+        h.remap_bytes = 0;
+    }
+    if (remap_kind == MPHF_REMAP_VEC) {
+        remap.p = F.release();
+        h.remap_bytes = len * 4;
+    }
+    h.remap = remap_kind;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(t1, s));
+    CK(cudaEventSynchronize(t1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    out->hdr = h;
+    out->d_pilots = static_cast<uint8_t *>(pilots.release());
+    out->d_remap = static_cast<uint8_t *>(remap.p ? remap.release() : nullptr);
+    if (!out->d_remap) {
+        cudaError_t e = cudaMalloc(&out->d_remap, 64);
+        if (e != cudaSuccess) { cudaFree(out->d_pilots); return cuda_fail(e, "remap placeholder"); }
+    }
+    out->evictions = evictions_total;
+    out->build_ms = ms;
+    return MPHF_OK;
+}
+
+}  // namespace ptrhash

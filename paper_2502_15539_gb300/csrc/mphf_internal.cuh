@@ -1,0 +1,144 @@
+// Internal declarations shared by the library's translation units.
+//
+// Device-side view of a PtrHash structure and the exact 64-bit integer
+// arithmetic of the query (Sec. 3.1 Eq. partbucket and Eq. slot, Sec. 3.3
+// gamma, Sec. 3.4 Eq. clef).  Everything here is integer and exact.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/mphf.h"
+
+namespace ptrhash {
+
+enum : int { kReducePow2 = 0, kReduceMod = 1 };
+enum : int { kRemapClef = MPHF_REMAP_CLEF, kRemapVec = MPHF_REMAP_VEC, kRemapNone = 2 };
+constexpr int kClefPerLine = 44;   // values per 64-byte CacheLineEF line (Sec. 3.4)
+
+// Everything a query kernel needs, passed by value as a kernel argument.
+struct View {
+    const uint8_t *pilots;   // P*B bytes
+    const void *remap;       // CacheLineEF lines (64 B each) or u32 entries
+    uint64_t n, P, S, B, C, seed;
+    uint64_t fm_hi, fm_lo;   // ceil(2^128 / S) for reduce = x mod S
+    uint64_t s_mask;         // S - 1 for power-of-two S
+};
+
+// ---------------------------------------------------------------- host side
+struct Header {
+    uint64_t n = 0, P = 0, S = 0, B = 0, C = 0, seed = 0;
+    int32_t gamma = MPHF_GAMMA_CUBIC, remap = MPHF_REMAP_CLEF, reduce = kReducePow2;
+    int32_t key_kind = MPHF_KEY_U64;
+    double lambda = 3.5, alpha = 0.99;
+    uint64_t remap_len = 0;    // P*S - n
+    uint64_t remap_bytes = 0;  // bytes of the remap payload
+};
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+void count_launch(uint64_t k = 1);
+
+// Layout rule of Sec. 3.1 "Parameter values" (library's own implementation).
+int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_override,
+                  uint64_t *P, uint64_t *S, uint64_t *B, int *reduce);
+void fastmod_constant(uint64_t S, uint64_t *hi, uint64_t *lo);
+uint64_t clef_lines_for(uint64_t remap_len);
+
+View make_view(const Header &h, const uint8_t *pilots, const void *remap);
+
+// Query launchers (mphf_query.cu).
+int launch_query_u64(const Header &h, const View &v, const uint64_t *keys, uint64_t count,
+                     uint32_t *out, bool phf, cudaStream_t s);
+int launch_query_bytes(const Header &h, const View &v, const uint8_t *bytes,
+                       const uint64_t *offsets, uint64_t count, uint32_t *out, cudaStream_t s);
+
+// Key hashes for the builder (mphf_query.cu).
+int launch_hash_keys(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t C,
+                     uint64_t seed, uint64_t *out, int sm_count, cudaStream_t s);
+
+// Builder (mphf_build.cu).  Fills header, pilots and remap on the device.
+struct BuildResult {
+    Header hdr;
+    uint8_t *d_pilots = nullptr;
+    uint8_t *d_remap = nullptr;
+    uint64_t evictions = 0;
+    double build_ms = 0.0;
+};
+int build_structure(const mphf_params &p, int key_kind, const void *keys, const uint64_t *offsets,
+                    uint64_t n, cudaStream_t s, BuildResult *out);
+
+// ------------------------------------------------------------- device side
+__device__ __forceinline__ uint64_t mul_hi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+// gamma on 64-bit fixed point (Sec. 3.3): gamma_1(x) = x, gamma_3(x) =
+// 255/256 (x^2 + x^3)/2 + x/256 with x^2 = hi(x x), x^3 = hi(x^2 x), floors.
+template <int GAMMA>
+__device__ __forceinline__ uint64_t bucket_fn(uint64_t x) {
+    if constexpr (GAMMA == MPHF_GAMMA_LINEAR) {
+        return x;
+    } else {
+        uint64_t sq = mul_hi(x, x);
+        uint64_t cube = mul_hi(sq, x);
+        uint64_t half = (sq >> 1) + (cube >> 1);
+        return half - (half >> 8) + (x >> 8);
+    }
+}
+
+// x mod S for S < 2^32 by direct computation of the remainder (Lemire,
+// Kaser, Kurz 2019): with c = ceil(2^128 / S), x mod S = ((c x mod 2^128) S) >> 128.
+__device__ __forceinline__ uint64_t mod_direct(uint64_t x, uint64_t c_hi, uint64_t c_lo,
+                                               uint64_t S) {
+    uint64_t l0 = c_lo * x;
+    uint64_t l1 = mul_hi(c_lo, x) + c_hi * x;   // (c x) mod 2^128 = (l1, l0)
+    uint64_t b1 = mul_hi(l0, S);
+    uint64_t d0 = l1 * S;
+    uint64_t d1 = mul_hi(l1, S);
+    return d1 + ((d0 + b1) < d0 ? 1u : 0u);
+}
+
+template <int REDUCE>
+__device__ __forceinline__ uint64_t reduce_slot(const View &v, uint64_t x) {
+    if constexpr (REDUCE == kReducePow2) {
+        return mul_hi(v.C, x) & v.s_mask;      // hi(C x) mod S, S = 2^k
+    } else {
+        return mod_direct(x, v.fm_hi, v.fm_lo, v.S);
+    }
+}
+
+// Position of the i-th (0-based) set bit of a 32-bit word that has > i set bits.
+__device__ __forceinline__ uint32_t select32(uint32_t w, uint32_t i) {
+    uint32_t pos = 0, c;
+    c = __popc(w & 0xFFFFu); if (i >= c) { i -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xFFu);   if (i >= c) { i -= c; w >>= 8;  pos += 8; }
+    c = __popc(w & 0xFu);    if (i >= c) { i -= c; w >>= 4;  pos += 4; }
+    c = __popc(w & 0x3u);    if (i >= c) { i -= c; w >>= 2;  pos += 2; }
+    c = w & 1u;              if (i >= c) { pos += 1; }
+    return pos;
+}
+
+// CacheLineEF lookup (Sec. 3.4): v = 256 (offset + select(i) - i) + low[i].
+// Line layout: bytes 0..15 the 128-bit bitmap (two little-endian words),
+// 16..19 the offset, 20..63 the low bytes.
+__device__ __forceinline__ uint32_t clef_get(const uint8_t *lines, uint32_t j) {
+    uint32_t line = j / kClefPerLine;
+    uint32_t i = j - line * kClefPerLine;
+    const uint8_t *L = lines + (uint64_t)line * 64;
+    uint4 head = __ldg(reinterpret_cast<const uint4 *>(L));        // bitmap words
+    uint32_t offset = __ldg(reinterpret_cast<const uint32_t *>(L + 16));
+    uint32_t low = __ldg(L + 20 + i);
+    uint32_t words[4] = {head.x, head.y, head.z, head.w};
+    uint32_t sel = 0, k = i;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        uint32_t c = __popc(words[q]);
+        if (k < c) { sel = 32 * q + select32(words[q], k); break; }
+        k -= c;
+    }
+    return 256u * (offset + sel - i) + low;
+}
+
+}  // namespace ptrhash

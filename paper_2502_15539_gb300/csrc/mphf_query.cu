@@ -1,0 +1,323 @@
+// Query kernels: MPHF evaluation over device-resident keys.
+//
+// Per key (Sec. 3.1, Eq. partbucket / Eq. slot; Sec. 3.4):
+//   h = C k (u64 keys) or the string hash (byte keys)
+//   part = hi(P h), x = lo(P h), b = part B + hi(B gamma(x))
+//   p = pilots[b]                       <- the one random HBM access per key
+//   s = part S + reduce(h xor C (p xor seed), S)
+//   out = s < n ? s : F[s - n]          <- CacheLineEF line, ~1% of keys
+//
+// Each thread owns K keys of a tile: all K keys are loaded (streaming,
+// evict-first), all K bucket indexes computed, then all K pilot bytes are
+// requested before any is used, so K gathers per thread are in flight.
+#include "mphf_internal.cuh"
+
+namespace ptrhash {
+
+constexpr int kThreads = 256;
+constexpr int kKeysPerThread = 8;
+
+template <int GAMMA>
+__device__ __forceinline__ uint64_t bucket_of(const View &v, uint64_t h, uint64_t &part) {
+    part = mul_hi(v.P, h);
+    const uint64_t x = v.P * h;            // lo(P h): position inside the part
+    return part * v.B + mul_hi(v.B, bucket_fn<GAMMA>(x));
+}
+
+template <int REDUCE, int REMAP, bool PHF>
+__device__ __forceinline__ uint32_t slot_value(const View &v, uint64_t h, uint64_t part, uint32_t pilot) {
+    const uint64_t x = h ^ (v.C * ((uint64_t)pilot ^ v.seed));   // h xor hp(p)
+    const uint64_t s = part * v.S + reduce_slot<REDUCE>(v, x);
+    if (PHF || s < v.n) return (uint32_t)s;
+    const uint32_t j = (uint32_t)(s - v.n);
+    if constexpr (REMAP == kRemapClef) return clef_get(static_cast<const uint8_t *>(v.remap), j);
+    else return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+}
+
+// VEC: keys 16-byte and out 8-byte aligned; pairs of keys per load / store.
+template <int GAMMA, int REDUCE, int REMAP, bool PHF, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+query_u64_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
+                 uint32_t *__restrict__ out) {
+    constexpr int K = kKeysPerThread;
+    const uint64_t tile = (uint64_t)blockIdx.x * (kThreads * K);
+    uint64_t h[K], part[K], b[K];
+    uint32_t p[K];
+    if (VEC && tile + kThreads * K <= count) {
+#pragma unroll
+        for (int j = 0; j < K / 2; j++) {
+            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + i));
+            h[2 * j] = v.C * (((uint64_t)kk.y << 32) | kk.x);
+            h[2 * j + 1] = v.C * (((uint64_t)kk.w << 32) | kk.z);
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) b[q] = bucket_of<GAMMA>(v, h[q], part[q]);
+#pragma unroll
+        for (int q = 0; q < K; q++) p[q] = __ldg(v.pilots + b[q]);
+#pragma unroll
+        for (int j = 0; j < K / 2; j++) {
+            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            uint2 o;
+            o.x = slot_value<REDUCE, REMAP, PHF>(v, h[2 * j], part[2 * j], p[2 * j]);
+            o.y = slot_value<REDUCE, REMAP, PHF>(v, h[2 * j + 1], part[2 * j + 1], p[2 * j + 1]);
+            __stcs(reinterpret_cast<uint2 *>(out + i), o);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+            h[q] = v.C * (i < count ? __ldcs(keys + i) : 0ull);
+            b[q] = bucket_of<GAMMA>(v, h[q], part[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+            p[q] = i < count ? __ldg(v.pilots + b[q]) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+            const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+            if (i < count) out[i] = slot_value<REDUCE, REMAP, PHF>(v, h[q], part[q], p[q]);
+        }
+    }
+}
+
+template <int GAMMA, int REDUCE, int REMAP, bool PHF>
+static int launch_u64_t(const View &v, const uint64_t *keys, uint64_t count, uint32_t *out, cudaStream_t s) {
+    const uint64_t per_block = (uint64_t)kThreads * kKeysPerThread;
+    const uint64_t blocks = (count + per_block - 1) / per_block;
+    if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
+    const bool vec = ((uintptr_t)keys % 16 == 0) && ((uintptr_t)out % 8 == 0);
+    if (vec)
+        query_u64_kernel<GAMMA, REDUCE, REMAP, PHF, true><<<(unsigned)blocks, kThreads, 0, s>>>(v, keys, count, out);
+    else
+        query_u64_kernel<GAMMA, REDUCE, REMAP, PHF, false><<<(unsigned)blocks, kThreads, 0, s>>>(v, keys, count, out);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "query_u64 launch");
+}
+
+template <int GAMMA, int REDUCE>
+static int dispatch_remap(const Header &h, const View &v, const uint64_t *keys, uint64_t count,
+                          uint32_t *out, bool phf, cudaStream_t s) {
+    if (phf) return launch_u64_t<GAMMA, REDUCE, kRemapNone, true>(v, keys, count, out, s);
+    if (h.remap == MPHF_REMAP_VEC) return launch_u64_t<GAMMA, REDUCE, kRemapVec, false>(v, keys, count, out, s);
+    return launch_u64_t<GAMMA, REDUCE, kRemapClef, false>(v, keys, count, out, s);
+}
+
+int launch_query_u64(const Header &h, const View &v, const uint64_t *keys, uint64_t count,
+                     uint32_t *out, bool phf, cudaStream_t s) {
+    const bool cubic = h.gamma == MPHF_GAMMA_CUBIC;
+    const bool pow2 = h.reduce == kReducePow2;
+    if (cubic && pow2) return dispatch_remap<MPHF_GAMMA_CUBIC, kReducePow2>(h, v, keys, count, out, phf, s);
+    if (cubic) return dispatch_remap<MPHF_GAMMA_CUBIC, kReduceMod>(h, v, keys, count, out, phf, s);
+    if (pow2) return dispatch_remap<MPHF_GAMMA_LINEAR, kReducePow2>(h, v, keys, count, out, phf, s);
+    return dispatch_remap<MPHF_GAMMA_LINEAR, kReduceMod>(h, v, keys, count, out, phf, s);
+}
+
+// ------------------------------------------------------------ string keys
+// Project string hash (the paper's GxHash is not specified in it):
+//   w_j = little-endian u64 of bytes [8j, 8j+8) zero-padded past len,
+//   acc = sum_j mix(w_j xor (seed + j K1)),  h = mix(acc xor len K2 xor seed),
+// mix = splitmix64 finalizer.  The sum lets every word be hashed on its own.
+__device__ __forceinline__ uint64_t str_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+constexpr uint64_t kStrK1 = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kStrK2 = 0xC2B2AE3D27D4EB4Full;
+
+__device__ __forceinline__ uint64_t str_finish(uint64_t acc, uint64_t len, uint64_t seed) {
+    return str_mix(acc ^ (len * kStrK2) ^ seed);
+}
+
+// Word j of a string that starts `start` bytes into an 8-byte-aligned buffer.
+__device__ __forceinline__ uint64_t load_word(const uint64_t *buf, uint64_t start, uint64_t j,
+                                              uint64_t len) {
+    const uint64_t pos = start + 8 * j;
+    const uint64_t a = pos >> 3;
+    const uint32_t sh = (uint32_t)(pos & 7) * 8;
+    uint64_t w = buf[a] >> sh;
+    if (sh) w |= buf[a + 1] << (64 - sh);
+    const uint64_t rem = len - 8 * j;
+    if (rem < 8) w &= (1ull << (8 * rem)) - 1;
+    return w;
+}
+
+__device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uint64_t a, uint64_t len,
+                                                       uint64_t seed) {
+    uint64_t acc = 0;
+    for (uint64_t j = 0; 8 * j < len; j++) {
+        uint64_t w = 0;
+        for (uint32_t t = 0; t < 8 && 8 * j + t < len; t++) w |= (uint64_t)__ldg(bytes + a + 8 * j + t) << (8 * t);
+        acc += str_mix(w ^ (seed + j * kStrK1));
+    }
+    return str_finish(acc, len, seed);
+}
+
+constexpr int kStrWarps = 8;                       // warps per block
+constexpr int kStrStage = 2048 + 32;               // staged bytes per warp
+
+// One string per thread.  The warp's 32 strings are contiguous in memory;
+// their byte range is staged into shared memory with 16-byte loads and each
+// lane hashes its string from there.  A warp whose range does not fit the
+// stage reads its bytes from global memory instead.
+template <int GAMMA, int REDUCE, int REMAP>
+__global__ void __launch_bounds__(kStrWarps * 32)
+query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                   const uint64_t count, uint32_t *__restrict__ out) {
+    __shared__ __align__(16) uint8_t stage[kStrWarps][kStrStage];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * kStrWarps + warp) * 32;
+    if (w0 >= count) return;
+    const uint64_t i = w0 + lane;
+    const uint64_t last = (w0 + 32 < count ? w0 + 32 : count);
+    const uint64_t lo = __ldg(offsets + w0), hi = __ldg(offsets + last);
+    const uint64_t a = i < count ? __ldg(offsets + i) : hi;
+    const uint64_t e = i < count ? __ldg(offsets + i + 1) : hi;
+    const uint64_t base = lo & ~15ull;
+    const bool staged = hi - base + 32 <= kStrStage;   // + one zeroed chunk
+    uint64_t h;
+    if (staged) {
+        const uint64_t nvec = (hi - base + 15) / 16;
+        uint4 *dst = reinterpret_cast<uint4 *>(stage[warp]);
+        for (uint64_t q = lane; q < nvec; q += 32) {
+            const uint64_t c0 = base + 16 * q;
+            if (c0 + 16 <= hi) {
+                dst[q] = __ldcs(reinterpret_cast<const uint4 *>(bytes + c0));
+            } else {   // the last chunk: read no byte past the end of the keys
+                uint8_t *d8 = stage[warp] + 16 * q;
+                for (int t = 0; t < 16; t++) d8[t] = c0 + t < hi ? __ldg(bytes + c0 + t) : 0;
+            }
+        }
+        if (lane == 0) dst[nvec] = make_uint4(0, 0, 0, 0);   // word a+1 may be read
+        __syncwarp();
+        const uint64_t *buf = reinterpret_cast<const uint64_t *>(stage[warp]);
+        const uint64_t len = e - a, start = a - base;
+        uint64_t acc = 0;
+        for (uint64_t j = 0; 8 * j < len; j++) acc += str_mix(load_word(buf, start, j, len) ^ (v.seed + j * kStrK1));
+        h = str_finish(acc, len, v.seed);
+    } else {
+        h = hash_string_global(bytes, a, e - a, v.seed);
+    }
+    if (i >= count) return;
+    uint64_t part;
+    const uint64_t b = bucket_of<GAMMA>(v, h, part);
+    const uint32_t p = __ldg(v.pilots + b);
+    out[i] = slot_value<REDUCE, REMAP, false>(v, h, part, p);
+}
+
+template <int GAMMA, int REDUCE, int REMAP>
+static int launch_bytes_t(const View &v, const uint8_t *bytes, const uint64_t *offsets, uint64_t count,
+                          uint32_t *out, cudaStream_t s) {
+    const uint64_t per_block = kStrWarps * 32;
+    const uint64_t blocks = (count + per_block - 1) / per_block;
+    if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
+    if ((uintptr_t)bytes % 16) {
+        set_error("byte keys need a 16-byte aligned buffer");
+        return MPHF_ERR_ARG;
+    }
+    query_bytes_kernel<GAMMA, REDUCE, REMAP><<<(unsigned)blocks, per_block, 0, s>>>(v, bytes, offsets, count, out);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "query_bytes launch");
+}
+
+int launch_query_bytes(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
+                       uint64_t count, uint32_t *out, cudaStream_t s) {
+    const bool cubic = h.gamma == MPHF_GAMMA_CUBIC, pow2 = h.reduce == kReducePow2;
+    const bool vec = h.remap == MPHF_REMAP_VEC;
+#define MPHF_BYTES_CASE(G, R)                                                            \
+    return vec ? launch_bytes_t<G, R, kRemapVec>(v, bytes, offsets, count, out, s)     \
+               : launch_bytes_t<G, R, kRemapClef>(v, bytes, offsets, count, out, s);
+    if (cubic && pow2) { MPHF_BYTES_CASE(MPHF_GAMMA_CUBIC, kReducePow2) }
+    if (cubic) { MPHF_BYTES_CASE(MPHF_GAMMA_CUBIC, kReduceMod) }
+    if (pow2) { MPHF_BYTES_CASE(MPHF_GAMMA_LINEAR, kReducePow2) }
+    MPHF_BYTES_CASE(MPHF_GAMMA_LINEAR, kReduceMod)
+#undef MPHF_BYTES_CASE
+}
+
+// Key hashes for the builder: h = C k for u64 keys, the string hash above
+// for byte keys (one thread per key).
+__global__ void hash_keys_kernel(int key_kind, const void *__restrict__ keys,
+                                 const uint64_t *__restrict__ offsets, uint64_t n, uint64_t C,
+                                 uint64_t seed, uint64_t *__restrict__ out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (key_kind == MPHF_KEY_U64) {
+            out[i] = C * __ldg(static_cast<const uint64_t *>(keys) + i);
+        } else {
+            const uint64_t a = __ldg(offsets + i), e = __ldg(offsets + i + 1);
+            out[i] = hash_string_global(static_cast<const uint8_t *>(keys), a, e - a, seed);
+        }
+    }
+}
+
+int launch_hash_keys(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t C,
+                     uint64_t seed, uint64_t *out, int sm_count, cudaStream_t s) {
+    const uint64_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < (uint64_t)sm_count * 16 ? (want ? want : 1) : (uint64_t)sm_count * 16);
+    hash_keys_kernel<<<blocks, 256, 0, s>>>(key_kind, keys, offsets, n, C, seed, out);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "hash keys launch");
+}
+
+// ----------------------------------------------------- gather roofline probe
+// The same tile shape and key stream as query_u64_kernel; each key picks a
+// uniformly random byte of the table by fast range of a mixed key.
+__global__ void __launch_bounds__(kThreads)
+gather_probe_kernel(const uint64_t *__restrict__ keys, const uint64_t count, const uint8_t *__restrict__ table,
+                    const uint64_t table_bytes, uint32_t *__restrict__ out) {
+    constexpr int K = kKeysPerThread;
+    constexpr uint64_t kMix = 0x9E3779B97F4A7C15ull;
+    const uint64_t tile = (uint64_t)blockIdx.x * (kThreads * K);
+    uint64_t idx[K];
+    uint32_t p[K];
+    if (tile + kThreads * K <= count) {
+#pragma unroll
+        for (int j = 0; j < K / 2; j++) {
+            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + i));
+            idx[2 * j] = mul_hi(kMix * (((uint64_t)kk.y << 32) | kk.x), table_bytes);
+            idx[2 * j + 1] = mul_hi(kMix * (((uint64_t)kk.w << 32) | kk.z), table_bytes);
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) p[q] = __ldg(table + idx[q]);
+#pragma unroll
+        for (int j = 0; j < K / 2; j++) {
+            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            __stcs(reinterpret_cast<uint2 *>(out + i), make_uint2(p[2 * j], p[2 * j + 1]));
+        }
+    } else {
+        for (uint64_t i = tile + threadIdx.x; i < count; i += kThreads)
+            out[i] = __ldg(table + mul_hi(kMix * __ldcs(keys + i), table_bytes));
+    }
+}
+
+}  // namespace ptrhash
+
+using namespace ptrhash;
+
+extern "C" int mphf_gather_probe(const uint64_t *keys_dev, uint64_t count, const uint8_t *table_dev,
+                                 uint64_t table_bytes, uint32_t *out_dev, void *stream) {
+    if (count == 0) return MPHF_OK;
+    if (!keys_dev || !table_dev || !out_dev || table_bytes == 0 || ((uintptr_t)keys_dev % 16) ||
+        ((uintptr_t)out_dev % 8)) {
+        set_error("gather probe: keys 16-byte aligned, out 8-byte aligned, table non-empty");
+        return MPHF_ERR_ARG;
+    }
+    const uint64_t per_block = (uint64_t)kThreads * kKeysPerThread;
+    const uint64_t blocks = (count + per_block - 1) / per_block;
+    if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
+    gather_probe_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(keys_dev, count, table_dev,
+                                                                             table_bytes, out_dev);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "gather probe launch");
+}

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libmphf.so (argument marshalling only).
+
+Every function here forwards to the C entry point of the same name declared
+in ``include/mphf.h``; all computation happens in the library's CUDA kernels.
+Tensors are torch tensors on the current CUDA device (or pinned host tensors
+for ``mphf_query_u64_host``); streams default to torch's current stream.
+If the library is missing this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmphf.so")
+
+MPHF_OK = 0
+MPHF_ERR_ARG = -1
+MPHF_ERR_OOM = -2
+MPHF_ERR_DUP_KEYS = -3
+MPHF_ERR_BUILD_FAILED = -4
+MPHF_ERR_FORMAT = -5
+MPHF_ERR_CUDA = -6
+MPHF_ERR_TIMEOUT = -7
+MPHF_ERR_OVERFULL = -8
+MPHF_ERR_CAPACITY = -9
+
+MPHF_KEY_U64 = 0
+MPHF_KEY_BYTES = 1
+MPHF_GAMMA_LINEAR = 1
+MPHF_GAMMA_CUBIC = 3
+MPHF_REMAP_CLEF = 0
+MPHF_REMAP_VEC = 1
+
+
+class MphfError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str):
+        super().__init__(f"{what} failed: {code} ({detail})")
+        self.code = code
+
+
+class mphf_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("gamma", ctypes.c_int32), ("remap", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("C", ctypes.c_uint64),
+                ("slots_override", ctypes.c_uint64), ("max_reseeds", ctypes.c_int32),
+                ("evict_mult", ctypes.c_uint32)]
+
+
+class mphf_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("P", ctypes.c_uint64), ("S", ctypes.c_uint64),
+                ("B", ctypes.c_uint64), ("C", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("gamma", ctypes.c_int32), ("remap", ctypes.c_int32), ("reduce", ctypes.c_int32),
+                ("key_kind", ctypes.c_int32), ("remap_len", ctypes.c_uint64),
+                ("pilot_bytes", ctypes.c_uint64), ("remap_bytes", ctypes.c_uint64),
+                ("bits_per_key", ctypes.c_double), ("evictions", ctypes.c_uint64),
+                ("build_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Exported symbols of include/mphf.h with their ctypes signatures.
+_vp, _u64, _i32, _sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
+SIGNATURES = {
+    "mphf_default_params": (_i32, [ctypes.POINTER(mphf_params)]),
+    "mphf_build": (_i32, [ctypes.POINTER(mphf_params), _i32, _vp, _vp, _u64, _vp, ctypes.POINTER(_vp)]),
+    "mphf_query_u64": (_i32, [_vp, _vp, _u64, _vp, _vp]),
+    "mphf_query_bytes": (_i32, [_vp, _vp, _vp, _u64, _vp, _vp]),
+    "mphf_query_u64_phf": (_i32, [_vp, _vp, _u64, _vp, _vp]),
+    "mphf_query_u64_host": (_i32, [_vp, _vp, _u64, _vp, _vp]),
+    "mphf_serialize": (_i32, [_vp, _vp, _sz, ctypes.POINTER(_sz)]),
+    "mphf_deserialize": (_i32, [_vp, _sz, ctypes.POINTER(_vp)]),
+    "mphf_info": (_i32, [_vp, ctypes.POINTER(mphf_info_t)]),
+    "mphf_free": (None, [_vp]),
+    "mphf_strerror": (ctypes.c_char_p, [_i32]),
+    "mphf_last_error": (ctypes.c_char_p, []),
+    "mphf_layout": (_i32, [ctypes.POINTER(mphf_params), _u64, ctypes.POINTER(mphf_info_t)]),
+    "mphf_gather_probe": (_i32, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "mphf_launch_count": (_u64, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libmphf.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with paper_2502_15539_gb300.build_ext.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != MPHF_OK:
+        lib = load()
+        raise MphfError(rc, what, f"{lib.mphf_strerror(rc).decode()}: {lib.mphf_last_error().decode()}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_ptr(t: torch.Tensor, dtype, what: str) -> int:
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+        raise ValueError(f"{what}: contiguous {dtype} CUDA tensor required")
+    return t.data_ptr()
+
+
+def _u64_dtype_ok(t: torch.Tensor) -> bool:
+    return t.dtype in (torch.int64, getattr(torch, "uint64", torch.int64))
+
+
+def mphf_default_params(**overrides) -> mphf_params:
+    p = mphf_params()
+    _check(load().mphf_default_params(ctypes.byref(p)), "mphf_default_params")
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
+    return p
+
+
+def mphf_layout(n: int, params: mphf_params | None = None) -> dict:
+    params = params or mphf_default_params()
+    info = mphf_info_t()
+    _check(load().mphf_layout(ctypes.byref(params), n, ctypes.byref(info)), "mphf_layout")
+    return info.as_dict()
+
+
+class MPHF:
+    """Owns one device-resident structure (mphf_t*)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().mphf_free(h)
+            self._h = None
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def info(self) -> dict:
+        return mphf_info(self)
+
+    def serialize(self) -> bytes:
+        return mphf_serialize(self)
+
+
+def mphf_build(keys: torch.Tensor, params: mphf_params | None = None, offsets: torch.Tensor | None = None,
+               stream=None) -> MPHF:
+    """u64 keys: int64 CUDA tensor; byte keys: uint8 tensor + int64 offsets (n+1)."""
+    params = params or mphf_default_params()
+    out = ctypes.c_void_p()
+    if offsets is None:
+        if not _u64_dtype_ok(keys):
+            raise ValueError("u64 keys must be an int64 tensor")
+        kind, kp, op, n = MPHF_KEY_U64, _dev_ptr(keys, keys.dtype, "keys"), None, keys.numel()
+    else:
+        kind, kp = MPHF_KEY_BYTES, _dev_ptr(keys, torch.uint8, "bytes")
+        op, n = _dev_ptr(offsets, torch.int64, "offsets"), offsets.numel() - 1
+    _check(load().mphf_build(ctypes.byref(params), kind, kp, op, n, _stream(stream), ctypes.byref(out)),
+           "mphf_build")
+    return MPHF(out.value)
+
+
+def mphf_query_u64(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+    kp = _dev_ptr(keys, keys.dtype, "keys") if _u64_dtype_ok(keys) else None
+    if kp is None:
+        raise ValueError("keys must be int64")
+    _check(load().mphf_query_u64(m.handle, kp, keys.numel(), _dev_ptr(out, torch.int32, "out"), _stream(stream)),
+           "mphf_query_u64")
+    return out
+
+
+def mphf_query_u64_phf(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+    _check(load().mphf_query_u64_phf(m.handle, _dev_ptr(keys, torch.int64, "keys"), keys.numel(),
+                                     _dev_ptr(out, torch.int32, "out"), _stream(stream)), "mphf_query_u64_phf")
+    return out
+
+
+def mphf_query_bytes(m: MPHF, data: torch.Tensor, offsets: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    cnt = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(cnt, dtype=torch.int32, device=offsets.device)
+    _check(load().mphf_query_bytes(m.handle, _dev_ptr(data, torch.uint8, "bytes"),
+                                   _dev_ptr(offsets, torch.int64, "offsets"), cnt,
+                                   _dev_ptr(out, torch.int32, "out"), _stream(stream)), "mphf_query_bytes")
+    return out
+
+
+def mphf_query_u64_host(m: MPHF, keys_host: torch.Tensor, out_host: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    """keys_host / out_host: CPU tensors (pinned for overlapped copies)."""
+    if keys_host.is_cuda or keys_host.dtype != torch.int64 or not keys_host.is_contiguous():
+        raise ValueError("keys_host: contiguous int64 CPU tensor required")
+    if out_host is None:
+        out_host = torch.empty(keys_host.numel(), dtype=torch.int32, pin_memory=keys_host.is_pinned())
+    _check(load().mphf_query_u64_host(m.handle, keys_host.data_ptr(), keys_host.numel(), out_host.data_ptr(),
+                                      _stream(stream)), "mphf_query_u64_host")
+    return out_host
+
+
+def mphf_serialize(m: MPHF) -> bytes:
+    lib = load()
+    need = ctypes.c_size_t()
+    _check(lib.mphf_serialize(m.handle, None, 0, ctypes.byref(need)), "mphf_serialize")
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib.mphf_serialize(m.handle, buf, need.value, ctypes.byref(need)), "mphf_serialize")
+    return buf.raw
+
+
+def mphf_deserialize(blob: bytes) -> MPHF:
+    out = ctypes.c_void_p()
+    _check(load().mphf_deserialize(blob, len(blob), ctypes.byref(out)), "mphf_deserialize")
+    return MPHF(out.value)
+
+
+def mphf_info(m: MPHF) -> dict:
+    info = mphf_info_t()
+    _check(load().mphf_info(m.handle, ctypes.byref(info)), "mphf_info")
+    return info.as_dict()
+
+
+def mphf_gather_probe(keys: torch.Tensor, table: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    _check(load().mphf_gather_probe(_dev_ptr(keys, torch.int64, "keys"), keys.numel(),
+                                    _dev_ptr(table, torch.uint8, "table"), table.numel(),
+                                    _dev_ptr(out, torch.int32, "out"), _stream(stream)), "mphf_gather_probe")
+    return out
+
+
+def mphf_launch_count() -> int:
+    return load().mphf_launch_count()

@@ -76,6 +76,11 @@ def u64_keys(n: int, seed: int = 0, device="cpu", start: int = 0) -> torch.Tenso
     return fmix64(i ^ _salt(seed, _STREAM_KEY))
 
 
+def u64_keys_at(idx: torch.Tensor, seed: int = 0) -> torch.Tensor:
+    """Keys of the given stream indexes (u64_keys(n)[idx] without building it)."""
+    return fmix64(idx ^ _salt(seed, _STREAM_KEY))
+
+
 def nonmember_u64_keys(m: int, n: int, seed: int = 0, device="cpu", start: int = 0) -> torch.Tensor:
     """m keys guaranteed absent from ``u64_keys(n, seed)``."""
     return u64_keys(m, seed, device, start=n + start)

@@ -1,0 +1,33 @@
+"""Shared helpers of the GPU tests (structures are built by the oracle, so no
+expected value comes from the CUDA path)."""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2502_15539_gb300 import workloads as W
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_15539_gb300 import build_ext, native
+    build_ext.build()
+    native.load()
+    return native
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_structure(n: int, key_seed: int = 0, **params) -> tuple[O.OracleMPHF, bytes]:
+    keys = W.as_uint64_numpy(W.u64_keys(n, key_seed))
+    threads = 16 if n >= 10**6 else 1
+    m = O.OracleMPHF.build_u64(keys, threads=threads, **params)
+    return m, m.serialize()
+
+
+def u32(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)

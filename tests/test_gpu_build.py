@@ -1,0 +1,98 @@
+"""The library's own GPU builder: every structure it builds must be a
+bijection onto [0, n) for its keys, whatever the layout (Sec. 3.2); its
+errors follow the same rules as the oracle's."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2502_15539_gb300 import workloads as W
+from tests.gpu_common import need_gpu, u32
+
+pytestmark = pytest.mark.gpu
+
+
+def check_bijection(N, m, keys_dev, n):
+    got = u32(N.mphf_query_u64(m, keys_dev))
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+
+
+BUILD_CASES = [
+    (1, {}), (2, {}), (23, {}), (1000, {}), (20_000, {}), (200_000, {}),
+    (10**6, {}), (10**6, {"lam": 3.0, "gamma": 1, "remap": 1}), (10**6, {"lam": 4.0}),
+    (30_000, {"slots_override": 2048, "alpha": 0.9}),
+    (30_000, {"slots_override": 3001, "alpha": 0.9}),
+    (5 * 10**6, {}),
+]
+
+
+@pytest.mark.parametrize("n,params", BUILD_CASES)
+def test_gpu_build_is_bijective(n, params):
+    N = need_gpu()
+    keys = W.u64_keys(n, 1).cuda()
+    m = N.mphf_build(keys, N.mphf_default_params(**params))
+    info = N.mphf_info(m)
+    assert info["n"] == n
+    check_bijection(N, m, keys, n)
+    other = W.nonmember_u64_keys(1000, n, 1).cuda()
+    assert u32(N.mphf_query_u64(m, other)).max() < n
+    # The serialized structure reloads to the same function.
+    m2 = N.mphf_deserialize(N.mphf_serialize(m))
+    assert np.array_equal(u32(N.mphf_query_u64(m2, keys)), u32(N.mphf_query_u64(m, keys)))
+
+
+def test_gpu_build_remap_invariants():
+    """Keys mapping to slots >= n go, in slot order, to the free slots < n (Sec. 3.4)."""
+    N = need_gpu()
+    n = 10**6
+    keys = W.u64_keys(n, 2).cuda()
+    m = N.mphf_build(keys)
+    slots = u32(N.mphf_query_u64_phf(m, keys)).astype(np.int64)
+    final = u32(N.mphf_query_u64(m, keys)).astype(np.int64)
+    assert len(np.unique(slots)) == n
+    hi = slots >= n
+    order = np.argsort(slots[hi])
+    taken = np.zeros(n, bool)
+    taken[slots[~hi]] = True
+    free = np.flatnonzero(~taken)
+    assert np.array_equal(final[hi][order], free)
+    assert np.array_equal(final[~hi], slots[~hi])
+
+
+def test_gpu_build_duplicates_rejected():
+    N = need_gpu()
+    keys = W.u64_keys(5000, 0)
+    keys[77] = keys[4000]
+    with pytest.raises(N.MphfError) as e:
+        N.mphf_build(keys.cuda())
+    assert e.value.code == N.MPHF_ERR_DUP_KEYS
+
+
+def test_gpu_build_eviction_cap():
+    """evict_mult = 0 forbids eviction; the default cap of 10 S lets it build."""
+    N = need_gpu()
+    keys = W.u64_keys(200_000, 4).cuda()
+    m = N.mphf_build(keys, N.mphf_default_params(max_reseeds=0))
+    assert N.mphf_info(m)["evictions"] > 0
+    check_bijection(N, m, keys, 200_000)
+    with pytest.raises(N.MphfError) as e:
+        N.mphf_build(keys, N.mphf_default_params(max_reseeds=0, evict_mult=0))
+    assert e.value.code == N.MPHF_ERR_BUILD_FAILED
+
+
+@pytest.mark.parametrize("n", [1, 100, 50_000])
+def test_gpu_build_strings_bijective(n):
+    N = need_gpu()
+    data, off = W.strings(torch.arange(n), seed=6)
+    m = N.mphf_build(data.cuda(), offsets=off.cuda())
+    got = u32(N.mphf_query_bytes(m, data.cuda(), off.cuda()))
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+
+
+def test_gpu_build_duplicate_strings_rejected():
+    N = need_gpu()
+    data, off = W.strings(torch.tensor([0, 1, 2, 3, 1]), seed=6)
+    with pytest.raises(N.MphfError) as e:
+        N.mphf_build(data.cuda(), N.mphf_default_params(max_reseeds=2), offsets=off.cuda())
+    assert e.value.code == N.MPHF_ERR_DUP_KEYS
