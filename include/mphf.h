@@ -180,6 +180,33 @@ int mphf_gather_probe(const uint64_t *keys_dev, uint64_t count,
                       const uint8_t *table_dev, uint64_t table_bytes,
                       uint32_t *out_dev, void *stream);
 
+/* ------------------------------------------------ build without allocating */
+/* Builds the structure of n <= 65536 distinct u64 keys like mphf_build, but
+ * allocates no device memory: all of its device working memory lives in one
+ * fixed 8 MiB array that is part of the library image, so every GPU that
+ * loads the library holds those 8 MiB until the process exits.  It serves
+ * callers that may not allocate device memory: code running under a
+ * framework that owns all device memory through its own pool and budget,
+ * threads where the device-wide synchronization of cudaMalloc/cudaFree would
+ * stall other streams, or processes whose device memory is fully committed.
+ * The paper has no counterpart; this is a deployment variant of the build.
+ *   keys_dev   n uint64_t (device, 8-byte aligned), 1 <= n <= 65536.
+ *   out_host   host buffer receiving the structure in the serialized format
+ *              of mphf_serialize (load it with mphf_deserialize); cap bytes.
+ *   needed     set to the serialized size (may be NULL).
+ * Synchronous on `stream`.  The result is byte-identical to
+ * mphf_serialize(mphf_build(...)) for the same keys and parameters.
+ * Errors: MPHF_ERR_CAPACITY if n or the layout exceeds the fixed array;
+ * MPHF_ERR_ARG if out_host is NULL or smaller than *needed (retry with a
+ * larger buffer); otherwise as mphf_build.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call on a device shares the one array and
+ * overwrites what the previous call left there, so calls that overlap on
+ * the GPU (from several host threads or streams) race: serialize them. */
+int mphf_build_u64_noalloc(const mphf_params *params, const uint64_t *keys_dev, uint64_t n,
+                           void *out_host, size_t cap, size_t *needed, void *stream);
+
 /* Number of kernel launches this library issued since it was loaded
  * (all entry points, all threads). */
 uint64_t mphf_launch_count(void);

@@ -692,3 +692,226 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
 }
 
 }  // namespace ptrhash
+
+// ------------------------------------------------- build without allocating
+// mphf_build_u64_noalloc: the same construction for small key sets, with all
+// device working memory carved out of one fixed, file-scope device array
+// instead of cudaMalloc.  The array is part of the library image, so every
+// GPU that loads the library holds its 8 MiB until the process exits.
+#include <string.h>
+
+#include <mutex>
+
+namespace ptrhash {
+
+constexpr uint64_t kNoAllocScratchBytes = 8ull << 20;   // 8 MiB per device
+constexpr uint64_t kNoAllocMaxKeys = 65536;
+constexpr uint64_t kNoAllocMaxParts = 1024;
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static uint8_t *g_noalloc_base[64] = {};
+
+// Device address of the scratch array on device `dev` (current).  In host
+// code the array's name is only a host-side stand-in, so the address is
+// looked up once per device and cached.
+static int noalloc_scratch(int dev, uint8_t **out) {
+    if (dev < 0 || dev >= 64) { set_error("device ordinal %d out of range", dev); return MPHF_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_base[dev] = static_cast<uint8_t *>(p);
+    }
+    *out = g_noalloc_base[dev];
+    return MPHF_OK;
+}
+
+struct Carve {   // bump allocation inside the scratch array
+    uint8_t *base;
+    uint64_t used = 0, cap;
+    template <class T> T *take(uint64_t bytes) {
+        const uint64_t off = (used + 255) & ~255ull;
+        if (off + bytes > cap) return nullptr;
+        used = off + (bytes ? bytes : 1);
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+static void put64(uint8_t *p, uint64_t v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static void put32(uint8_t *p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+
+static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t n, cudaStream_t s,
+                         uint8_t *out, uint64_t cap, uint64_t *needed) {
+    if (n > kNoAllocMaxKeys) {
+        set_error("n=%llu is above the %llu keys this entry point supports", (unsigned long long)n,
+                  (unsigned long long)kNoAllocMaxKeys);
+        return MPHF_ERR_CAPACITY;
+    }
+    if (!(prm.C & 1)) { set_error("mixing constant C must be odd"); return MPHF_ERR_ARG; }
+    if (prm.gamma != MPHF_GAMMA_LINEAR && prm.gamma != MPHF_GAMMA_CUBIC) { set_error("bad gamma"); return MPHF_ERR_ARG; }
+    if (prm.remap != MPHF_REMAP_CLEF && prm.remap != MPHF_REMAP_VEC) { set_error("bad remap kind"); return MPHF_ERR_ARG; }
+    uint64_t P, S, B;
+    int reduce;
+    int rc = choose_layout(n, prm.lambda, prm.alpha, prm.slots_override, &P, &S, &B, &reduce);
+    if (rc) return rc;
+    if (S > kMaxSlots || P > kNoAllocMaxParts) {
+        set_error("layout P=%llu S=%llu exceeds this entry point's limits", (unsigned long long)P, (unsigned long long)S);
+        return MPHF_ERR_CAPACITY;
+    }
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint8_t *base = nullptr;
+    rc = noalloc_scratch(dev, &base);
+    if (rc) return rc;
+
+    const uint64_t total = P * S, nbkt = P * B, words = (total + 31) / 32, len = total - n;
+    const uint64_t lines = clef_lines_for(len);
+    const unsigned search_grid = (unsigned)(P < (uint64_t)sms ? P : (uint64_t)sms);
+    size_t sort_tmp = 0, scan_tmp = 0;
+    CK(cub::DeviceRadixSort::SortKeys(nullptr, sort_tmp, (const uint64_t *)nullptr, (uint64_t *)nullptr, n, 0, 64, s));
+    CK(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, (const uint32_t *)nullptr, (uint32_t *)nullptr, words, s));
+    Carve c{base, 0, kNoAllocScratchBytes};
+    uint64_t *hash = c.take<uint64_t>(n * 8), *sorted = c.take<uint64_t>(n * 8);
+    void *sort_buf = c.take<void>(sort_tmp), *scan_buf = c.take<void>(scan_tmp);
+    uint32_t *bstart = c.take<uint32_t>((nbkt + 1) * 4);
+    uint8_t *pilots = c.take<uint8_t>(nbkt);
+    uint32_t *taken = c.take<uint32_t>((words + 1) * 4);
+    uint32_t *owner = c.take<uint32_t>((uint64_t)search_grid * S * 4);
+    uint32_t *order = c.take<uint32_t>((uint64_t)search_grid * B * 4);
+    uint32_t *status = c.take<uint32_t>(P * 4);
+    uint32_t *flags = c.take<uint32_t>(64);
+    uint32_t *free_cnt = c.take<uint32_t>(words * 4), *high_cnt = c.take<uint32_t>(words * 4);
+    uint32_t *free_rank = c.take<uint32_t>((words + 1) * 4), *high_rank = c.take<uint32_t>((words + 1) * 4);
+    uint32_t *L = c.take<uint32_t>(len * 4), *F = c.take<uint32_t>(len * 4);
+    uint8_t *lines_buf = c.take<uint8_t>(lines * 64);
+    if (!lines_buf || !F || !L || !high_rank || !free_rank || !high_cnt || !free_cnt || !flags || !status || !order ||
+        !owner || !taken || !pilots || !bstart || !scan_buf || !sort_buf || !sorted || !hash) {
+        set_error("this layout needs more than the %llu-byte scratch array", (unsigned long long)kNoAllocScratchBytes);
+        return MPHF_ERR_CAPACITY;
+    }
+
+    const size_t smem = kMaxBucket * 8 + ((S + 31) / 32) * 4 + (kMaxBucket + 1) * 4 + kSetSize * 4 + kPendingCap * 4 + 16 * 4;
+    Header h;
+    h.n = n; h.P = P; h.S = S; h.B = B; h.C = prm.C; h.gamma = prm.gamma; h.reduce = reduce;
+    h.key_kind = MPHF_KEY_U64; h.lambda = prm.lambda; h.alpha = prm.alpha; h.remap_len = len;
+    bool built = false;
+    int last_fail = MPHF_ERR_BUILD_FAILED;
+    const int attempts = prm.max_reseeds < 0 ? 1 : prm.max_reseeds + 1;
+    uint32_t st[kNoAllocMaxParts];
+    for (int attempt = 0; attempt < attempts && !built; attempt++) {
+        const uint64_t seed = prm.seed + (uint64_t)attempt;
+        h.seed = seed;
+        CK(cudaMemsetAsync(flags, 0, 64, s));
+        rc = launch_hash_keys(MPHF_KEY_U64, keys, nullptr, n, prm.C, seed, hash, sms, s);
+        if (rc) return rc;
+        CK(cub::DeviceRadixSort::SortKeys(sort_buf, sort_tmp, hash, sorted, n, 0, 64, s));
+        count_launch(4);
+        if (prm.gamma == MPHF_GAMMA_CUBIC)
+            bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, bstart, flags);
+        else
+            bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, bstart, flags);
+        part_size_kernel<<<grid_for(P, sms), 256, 0, s>>>(bstart, P, B, S, flags + 1);
+        count_launch(2);
+        CK(cudaGetLastError());
+        uint32_t hf[2];
+        CK(cudaMemcpyAsync(hf, flags, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hf[0]) { set_error("equal key hashes (duplicate keys)"); return MPHF_ERR_DUP_KEYS; }
+        if (hf[1]) { set_error("a part holds more than S=%llu keys", (unsigned long long)S); return MPHF_ERR_OVERFULL; }
+        CK(cudaMemsetAsync(taken, 0, (words + 1) * 4, s));
+        CK(cudaMemsetAsync(pilots, 0, nbkt, s));
+        SearchArgs a;
+        a.sorted = sorted; a.bstart = bstart; a.pilots = pilots; a.taken = taken; a.owner_scratch = owner;
+        a.order_scratch = order; a.status = status;
+        a.evictions = reinterpret_cast<unsigned long long *>(flags + 4);
+        a.next_part = flags + 2;
+        a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;
+        a.fm_hi = a.fm_lo = 0;
+        if (reduce == kReduceMod) fastmod_constant(S, &a.fm_hi, &a.fm_lo);
+        a.evict_cap = (uint64_t)prm.evict_mult * S;
+        CK(reduce == kReducePow2 ? launch_search<kReducePow2>(a, search_grid, smem, s)
+                                 : launch_search<kReduceMod>(a, search_grid, smem, s));
+        CK(cudaMemcpyAsync(st, status, P * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        uint64_t failed = 0;
+        for (uint64_t p = 0; p < P; p++) failed += st[p] != kPartOk;
+        if (failed) {
+            set_error("%llu part(s) failed with seed %llu", (unsigned long long)failed, (unsigned long long)seed);
+            continue;
+        }
+        built = true;
+    }
+    if (!built) return last_fail;
+
+    remap_count_kernel<<<grid_for(words, sms), 256, 0, s>>>(taken, words, n, total, free_cnt, high_cnt);
+    count_launch();
+    CK(cub::DeviceScan::ExclusiveSum(scan_buf, scan_tmp, free_cnt, free_rank, words, s));
+    CK(cub::DeviceScan::ExclusiveSum(scan_buf, scan_tmp, high_cnt, high_rank, words, s));
+    count_launch(2);
+    uint32_t tail[4];
+    CK(cudaMemcpyAsync(&tail[0], free_rank + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tail[1], free_cnt + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tail[2], high_rank + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tail[3], high_cnt + words - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t R = (uint64_t)tail[0] + tail[1];
+    if (R != (uint64_t)tail[2] + tail[3]) { set_error("internal: remap counts differ"); return MPHF_ERR_BUILD_FAILED; }
+    free_list_kernel<<<grid_for(words, sms), 256, 0, s>>>(taken, words, n, free_rank, L);
+    remap_values_kernel<<<grid_for(len, sms), 256, 0, s>>>(taken, high_rank, L, n, total, R, F);
+    count_launch(2);
+    h.remap = prm.remap;
+    const uint8_t *remap_src = reinterpret_cast<const uint8_t *>(F);
+    h.remap_bytes = len * 4;
+    if (prm.remap == MPHF_REMAP_CLEF) {
+        h.remap_bytes = lines * 64;
+        remap_src = lines_buf;
+        if (len > 0) {
+            clef_encode_kernel<<<grid_for(lines, sms), 256, 0, s>>>(F, len, lines, lines_buf, flags + 3);
+            count_launch();
+            uint32_t span_fail = 0;
+            CK(cudaMemcpyAsync(&span_fail, flags + 3, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (span_fail) { h.remap = MPHF_REMAP_VEC; h.remap_bytes = len * 4; remap_src = reinterpret_cast<const uint8_t *>(F); }
+        }
+    }
+    CK(cudaGetLastError());
+    const uint64_t pad_pilots = (nbkt + 63) & ~63ull;
+    const uint64_t need = 128 + pad_pilots + h.remap_bytes;
+    if (needed) *needed = need;
+    if (!out || cap < need) { set_error("output buffer of %llu bytes, %llu needed", (unsigned long long)cap, (unsigned long long)need); return MPHF_ERR_ARG; }
+    memset(out, 0, 128 + pad_pilots);
+    memcpy(out, "PTRHASH1", 8);
+    put32(out + 8, 1);
+    put32(out + 12, MPHF_KEY_U64);
+    put32(out + 16, (uint32_t)h.gamma);
+    put32(out + 20, (uint32_t)h.remap);
+    put32(out + 24, (uint32_t)h.reduce);
+    put64(out + 32, n); put64(out + 40, P); put64(out + 48, S); put64(out + 56, B);
+    put64(out + 64, h.C); put64(out + 72, h.seed); put64(out + 80, len); put64(out + 88, h.remap_bytes);
+    uint64_t lb, ab;
+    memcpy(&lb, &h.lambda, 8); memcpy(&ab, &h.alpha, 8);
+    put64(out + 96, lb); put64(out + 104, ab); put64(out + 112, nbkt);
+    CK(cudaMemcpyAsync(out + 128, pilots, nbkt, cudaMemcpyDeviceToHost, s));
+    if (h.remap_bytes) CK(cudaMemcpyAsync(out + 128 + pad_pilots, remap_src, h.remap_bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MPHF_OK;
+}
+
+}  // namespace ptrhash
+
+extern "C" int mphf_build_u64_noalloc(const mphf_params *params, const uint64_t *keys_dev, uint64_t n,
+                                      void *out_host, size_t cap, size_t *needed, void *stream) {
+    if (!params || !keys_dev || ((uintptr_t)keys_dev & 7)) {
+        ptrhash::set_error("NULL params or keys, or keys not 8-byte aligned");
+        return MPHF_ERR_ARG;
+    }
+    uint64_t need = 0;
+    int rc = ptrhash::build_noalloc(*params, keys_dev, n, (cudaStream_t)stream, static_cast<uint8_t *>(out_host),
+                                    cap, &need);
+    if (needed) *needed = need;
+    return rc;
+}

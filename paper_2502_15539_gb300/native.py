@@ -81,6 +81,8 @@ SIGNATURES = {
     "mphf_layout": (_i32, [ctypes.POINTER(mphf_params), _u64, ctypes.POINTER(mphf_info_t)]),
     "mphf_gather_probe": (_i32, [_vp, _u64, _vp, _u64, _vp, _vp]),
     "mphf_launch_count": (_u64, []),
+    "mphf_build_u64_noalloc": (_i32, [ctypes.POINTER(mphf_params), _vp, _u64, _vp, _sz, ctypes.POINTER(_sz),
+                                      _vp]),
 }
 
 _lock = threading.Lock()
@@ -255,3 +257,22 @@ def mphf_gather_probe(keys: torch.Tensor, table: torch.Tensor, out: torch.Tensor
 
 def mphf_launch_count() -> int:
     return load().mphf_launch_count()
+
+
+def mphf_build_u64_noalloc(keys: torch.Tensor, params: mphf_params | None = None, stream=None) -> bytes:
+    """Builds without allocating device memory (n <= 65536); returns the
+    serialized structure, as mphf_serialize would."""
+    params = params or mphf_default_params()
+    lib = load()
+    n = keys.numel()
+    cap = 128 + n * 8 + 4096
+    need = ctypes.c_size_t()
+    buf = ctypes.create_string_buffer(cap)
+    rc = lib.mphf_build_u64_noalloc(ctypes.byref(params), _dev_ptr(keys, torch.int64, "keys"), n, buf, cap,
+                                    ctypes.byref(need), _stream(stream))
+    if rc == MPHF_ERR_ARG and need.value > cap:
+        buf = ctypes.create_string_buffer(need.value)
+        rc = lib.mphf_build_u64_noalloc(ctypes.byref(params), _dev_ptr(keys, torch.int64, "keys"), n, buf,
+                                        need.value, ctypes.byref(need), _stream(stream))
+    _check(rc, "mphf_build_u64_noalloc")
+    return buf.raw[:need.value]
