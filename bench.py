@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1 << 26, help="oracle baseline sample (keys)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--query-keys", type=int, default=0,
+                    help="query a seeded sample of this many member keys per step instead of all n "
+                         "(small profiling case against the full-size structure)")
     return ap.parse_args()
 
 
@@ -154,18 +157,23 @@ def run_gpu(args):
     keys = W.u64_keys(n, seed=0, device=dev)
     m = N.mphf_build(keys)
     info = N.mphf_info(m)
-    perm = W.permutation(n, seed=1 + rank, device=dev)
-    q = keys[perm]
-    del perm
+    if 0 < args.query_keys < n:
+        mq = args.query_keys
+        del keys
+        torch.cuda.empty_cache()
+        q = W.u64_keys_at(W.uniform_index(mq, n, seed=1 + rank, device=dev), seed=0)
+    else:
+        mq = n
+        perm = W.permutation(n, seed=1 + rank, device=dev)
+        q = keys[perm]
+        del perm, keys
     torch.cuda.empty_cache()
-    out = torch.empty(n, dtype=torch.int32, device=dev)
+    out = torch.empty(mq, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
     # Fraction of keys whose slot is >= n (they read one CacheLineEF line).
     N.mphf_query_u64_phf(m, q, out)
     remapped = int(((out.to(torch.int64) & 0xFFFFFFFF) >= n).sum().item())
-    del keys
-    torch.cuda.empty_cache()
 
     def time_steps(fn, k):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
@@ -197,7 +205,7 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = ws * n * args.steps / (total_ms / 1e3)
+    value = ws * mq * args.steps / (total_ms / 1e3)
 
     # Random-gather probe: same key stream, table the size of the pilot array.
     table = torch.randint(0, 256, (info["pilot_bytes"],), dtype=torch.uint8, device=dev)
@@ -210,17 +218,17 @@ def run_gpu(args):
     # Roofline of the query kernel (HBM bound): algorithmic bytes per key =
     # 8 (key) + 4 (result) + 32 (the pilot's DRAM sector) + 64 per remapped key.
     peak, peak_kind = measured_peaks()
-    alg_bytes = n * (8 + 4 + 32) + remapped * 64
+    alg_bytes = mq * (8 + 4 + 32) + remapped * 64
     kernel_ms = statistics.mean(per_step)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = recorded_traffic(n)
+    traffic = recorded_traffic(mq)
 
     # End to end through the C ABI with pinned host buffers.
     e2e = None
     if not args.no_e2e:
-        qh = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        qh = torch.empty(mq, dtype=torch.int64, pin_memory=True)
         qh.copy_(q)
-        oh = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        oh = torch.empty(mq, dtype=torch.int32, pin_memory=True)
         for _ in range(max(1, args.warmup)):
             N.mphf_query_u64_host(m, qh, oh)
         barrier()
@@ -232,8 +240,8 @@ def run_gpu(args):
         tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         if ws > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": ws * n * args.steps / float(tt.item()), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n,
+        e2e = {"value": ws * mq * args.steps / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * mq, "d2h_bytes_per_step": 4 * mq,
                "ms_per_step": 1e3 * float(tt.item()) / args.steps}
         del qh, oh
 
@@ -246,21 +254,23 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"plain at scale: n={n} distinct u64 keys, query all n in a seeded random order",
+            "config": {"workload": (f"plain at scale: n={n} distinct u64 keys, query all n in a seeded random order"
+                                    if mq == n else f"profiling case: n={n} structure, {mq} sampled member keys"),
                        "n": n, "params": "Default (gamma_3, lambda 3.5, alpha 0.99, CacheLineEF)",
                        "P": info["P"], "S": info["S"], "B": info["B"], "bits_per_key": info["bits_per_key"],
                        "l2": "inputs larger than L2 (8 GB keys + 4 GB out per step, 286 MB pilots)",
                        "parallelism": f"replicas x{ws}"},
             "ns_per_key": 1e9 / (value / ws),
+            "query_keys_per_step": mq,
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind, "alg_bytes_per_key": alg_bytes / n,
+                         "peak_kind": peak_kind, "alg_bytes_per_key": alg_bytes / mq,
                          "kernel": "query_u64_kernel"},
             "gather_roofline": {"probe_ms": probe_ms, "query_ms": kernel_ms, "frac": probe_ms / kernel_ms,
                                 "probe": "mphf_gather_probe: same key stream, 1 random byte of a "
                                          f"{info['pilot_bytes']}-byte table per key"},
-            "remapped_fraction": remapped / n,
+            "remapped_fraction": remapped / mq,
             "build": {"ms": info["build_ms"], "ns_per_key": 1e6 * info["build_ms"] / n,
                       "evictions": info["evictions"]},
             "clocks": clocks,
