@@ -476,6 +476,22 @@ static int build_part(const build_ctx *bc, part_state *ps, uint64_t part,
                 if (blocked) continue;
                 if (cost < best_cost) { best_cost = cost; chosen = p; }
             }
+            if (chosen < 0) {
+                /* Reading: the tabu only exists to break eviction cycles; when
+                 * it blocks every pilot that does not self-collide, it is
+                 * ignored for this bucket.  Only a bucket whose every pilot
+                 * self-collides fails the part. */
+                for (int p = 0; p < 256; p++) {
+                    bucket_slots(bc, ps, b, (uint64_t)p, slots);
+                    if (self_collides(slots, s)) continue;
+                    uint64_t cost = 0;
+                    for (uint64_t j = 0; j < s; j++) {
+                        uint32_t o = ps->owner[slots[j]];
+                        if (o != NONE32) cost += bsize(ps, o) * bsize(ps, o);
+                    }
+                    if (cost < best_cost) { best_cost = cost; chosen = p; }
+                }
+            }
             if (chosen < 0) { rc = ORC_ERR_BUILD; break; }
             bucket_slots(bc, ps, b, (uint64_t)chosen, slots);
             for (uint64_t j = 0; j < s; j++) {

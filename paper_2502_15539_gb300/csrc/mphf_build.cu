@@ -10,7 +10,8 @@
 //      whose keys land on distinct free slots; else the pilot of least
 //      weighted collisions (weight s^2 for a key of a bucket of size s),
 //      evicting the colliding buckets, never one of the 16 most recently
-//      placed; a part fails after evict_mult * S evictions  (pilot_search_kernel)
+//      placed unless that blocks every pilot; a part fails after
+//      evict_mult * S evictions                              (pilot_search_kernel)
 //   5. remap: the R taken slots >= n in order go to the R free slots < n in
 //      order, F[q - n]; other entries repeat their predecessor; CacheLineEF
 //      encoding of F, or a plain u32 array if a line's span does not fit.
@@ -183,7 +184,7 @@ __device__ __forceinline__ uint64_t bucket_size(const SearchArgs &a, uint64_t gb
 // the smaller pilot.  Returns -1 if no pilot is allowed.
 template <int REDUCE>
 __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const uint32_t *owner, uint64_t gb0,
-                            uint64_t myh, int s, uint32_t &gen, int lane) {
+                            uint64_t myh, int s, uint32_t &gen, int lane, bool use_tabu) {
     uint64_t best_cost = ~0ull;
     int best_p = -1;
     if (s <= kSmallBucket) {
@@ -200,7 +201,7 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
                     sl[j] = slot_in_part<REDUCE>(a, hj ^ hp);
                     if (bit_of(sh.bits, sl[j])) {
                         const uint32_t o = owner[sl[j]];
-                        if (in_recent(sh.recent, o)) ok = false;
+                        if (use_tabu && in_recent(sh.recent, o)) ok = false;
                         const uint64_t z = bucket_size(a, gb0, o);
                         cost += z * z;
                     }
@@ -232,7 +233,7 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
             if (!set_insert(sh.set, sl, gen)) bad = true;
             else if (bit_of(sh.bits, sl)) {
                 const uint32_t o = owner[sl];
-                if (in_recent(sh.recent, o)) bad = true;
+                if (use_tabu && in_recent(sh.recent, o)) bad = true;
                 const uint64_t z = bucket_size(a, gb0, o);
                 cost += z * z;
             }
@@ -290,7 +291,10 @@ __device__ uint32_t search_part(const SearchArgs &a, const SearchShared &sh, uin
         int chosen = s <= kSmallBucket ? greedy_small<REDUCE>(a, sh.bits, myh, s, lane)
                                        : greedy_large<REDUCE>(a, sh, s, gen, lane);
         if (chosen < 0) {
-            chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane);
+            chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, true);
+            // The tabu only breaks eviction cycles: when it blocks every pilot
+            // that does not self-collide, it is ignored for this bucket.
+            if (chosen < 0) chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, false);
             if (chosen < 0) return kPartNoPilot;
             const uint64_t hp = a.C * ((uint64_t)chosen ^ a.seed);
             for (int j = 0; j < s; j++) {
