@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1 << 26, help="oracle baseline sample (keys)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-mphfs", type=int, default=256)
     ap.add_argument("--query-keys", type=int, default=0,
                     help="query a seeded sample of this many member keys per step instead of all n "
                          "(small profiling case against the full-size structure)")
@@ -248,6 +250,9 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, q, args.cpu_sample)
+    del q, out
+    torch.cuda.empty_cache()
+    batched = None if args.no_batched else run_batched(args, dev, stream)
 
     if rank == 0:
         line = {
@@ -276,10 +281,73 @@ def run_gpu(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args, dev, stream):
+    """Many structures in one persistent launch: 256 structures with n
+    log-uniform in [1e3, 1e7] (seed 2), one request each of log-uniform size
+    in [1, 1e6] (seed 3), 90% member and 10% non-member keys.  Timed: one
+    graph-replayed persistent launch per step (autotuned shape) against one
+    plain mphf_query_u64 launch per request."""
+    import torch
+    from paper_2502_15539_gb300 import native as N
+    from paper_2502_15539_gb300 import workloads as W
+
+    k = args.batch_mphfs
+    ns = W.log_uniform_int(k, 1e3, 1e7, seed=2).tolist()
+    qs = W.log_uniform_int(k, 1, 1e6, seed=3).tolist()
+    structs, items = [], []
+    build_ms = 0.0
+    for i, (n, qn) in enumerate(zip(ns, qs)):
+        keys = W.u64_keys(n, seed=1000 + i, device=dev)
+        m = N.mphf_build(keys)
+        build_ms += N.mphf_info(m)["build_ms"]
+        nm = qn // 10
+        q = torch.cat([keys[W.uniform_index(qn - nm, n, seed=2000 + i, device=dev)],
+                       W.nonmember_u64_keys(nm, n, seed=1000 + i, device=dev)])
+        del keys
+        structs.append(m)
+        items.append((m, q, torch.empty(qn, dtype=torch.int32, device=dev)))
+    torch.cuda.empty_cache()
+    total = sum(qs)
+    arr, keep = N.make_requests(items)
+    b = N.Batch(k)
+    tuned = b.autotune(arr, k, os.path.join(tempfile.gettempdir(), "mphf_batch_tune.jsonl"), stream=stream)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / args.steps
+
+    batch_ms = timed(lambda: b.run(arr, k, stream=stream))
+    plain_ms = timed(lambda: [N.mphf_query_u64(m, q, o, stream=stream) for m, q, o in items])
+    # The batched outputs equal the per-request outputs (both parity-tested).
+    b.run(arr, k, stream=stream)
+    torch.cuda.synchronize()
+    got = [o.clone() for _, _, o in items]
+    for m, q, o in items:
+        N.mphf_query_u64(m, q, o, stream=stream)
+    torch.cuda.synchronize()
+    same = all(torch.equal(g, o) for g, (_, _, o) in zip(got, items))
+    return {"workload": f"{k} structures, n log-uniform [1e3, 1e7] (sum {sum(ns)}), requests log-uniform "
+                        f"[1, 1e6] (sum {total}), 90% members",
+            "queries_per_s": total / (batch_ms / 1e3), "ms_per_batch": batch_ms,
+            "per_request_launches": {"queries_per_s": total / (plain_ms / 1e3), "ms_per_batch": plain_ms},
+            "speedup": plain_ms / batch_ms, "autotuned": tuned, "outputs_identical": same,
+            "build_ms_total": build_ms}
 
 
 def cpu_baseline(m, q, sample: int):

@@ -130,12 +130,15 @@ int mphf_query_bytes(const mphf_t *m, const uint8_t *bytes_dev,
 int mphf_query_u64_phf(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
                        uint32_t *out_dev, void *stream);
 
-/* End-to-end query from host memory: copies the keys to the device in
- * chunks, evaluates them and copies the results back, overlapping the
- * copies with the kernels on `stream` and an internal copy stream.
+/* End-to-end query from host memory.  When both buffers are page-locked
+ * and mapped (cudaHostAlloc, cudaHostRegister), the kernel reads the keys
+ * and writes the results across the host link directly.  Otherwise the keys
+ * are copied to the device in chunks, evaluated, and the results copied
+ * back, overlapping the copies with the kernels on `stream` and two
+ * internal copy streams (staging buffers owned by the structure, allocated
+ * on first use).
  * keys_host: count uint64_t (host); out_host: count uint32_t (host).
- * Returns when every result is in out_host (synchronous).  Uses staging
- * buffers owned by the structure (allocated on first use).  Errors:
+ * Returns when every result is in out_host (synchronous).  Errors:
  * MPHF_ERR_ARG, MPHF_ERR_OOM, MPHF_ERR_CUDA. */
 int mphf_query_u64_host(mphf_t *m, const uint64_t *keys_host, uint64_t count,
                         uint32_t *out_host, void *stream);
@@ -179,6 +182,59 @@ int mphf_layout(const mphf_params *params, uint64_t n, mphf_info_t *out);
 int mphf_gather_probe(const uint64_t *keys_dev, uint64_t count,
                       const uint8_t *table_dev, uint64_t table_bytes,
                       uint32_t *out_dev, void *stream);
+
+/* --------------------------------------------------- multi-MPHF batches */
+/* One request of a batch: `count` keys of structure m.  For u64 structures
+ * keys_dev holds count uint64_t and offsets_dev is NULL; for byte-key
+ * structures keys_dev holds packed bytes and offsets_dev count+1 uint64_t.
+ * out_dev receives count uint32_t.  All device pointers, caller-owned. */
+typedef struct {
+    const mphf_t   *m;
+    const void     *keys_dev;
+    const uint64_t *offsets_dev;
+    uint64_t        count;          /* < 2^32 */
+    uint32_t       *out_dev;
+} mphf_request;
+
+/* Launch shape of the persistent batch kernel. */
+typedef struct {
+    int32_t keys_per_thread;  /* 2, 4, 8 or 16 gathers in flight per thread  */
+    int32_t threads;          /* 128, 256 or 512 threads per CTA             */
+    int32_t blocks_per_sm;    /* 1..16 persistent CTAs per SM                */
+    int32_t use_graph;        /* replay a captured CUDA graph (1) or launch  */
+} mphf_batch_config;
+
+typedef struct mphf_batch mphf_batch_t;
+
+/* A batch executor for up to max_requests (<= 4096) requests per run: one
+ * persistent kernel launch per run evaluates every request, whatever its
+ * structure and size (the paper's query_all over many structures, App. A;
+ * no paper counterpart for the multi-structure dispatch).  Owns two staging
+ * sets (page-locked host + device descriptor buffers) and their graphs.
+ * Default shape: 8 keys per thread, 256 threads, 4 CTAs per SM, graphs on. */
+int mphf_batch_create(uint32_t max_requests, mphf_batch_t **out);
+
+/* Evaluates every request; results are identical to mphf_query_u64 /
+ * mphf_query_bytes on each request.  Asynchronous on `stream`: returns once
+ * the work is queued (waits only for the run two calls back, whose staging
+ * set it reuses).  The structures and buffers must stay valid until the
+ * stream reaches this point.  Errors: MPHF_ERR_ARG, MPHF_ERR_CAPACITY,
+ * MPHF_ERR_CUDA. */
+int mphf_batch_run(mphf_batch_t *b, const mphf_request *reqs, uint32_t nreq, void *stream);
+
+int mphf_batch_set_config(mphf_batch_t *b, const mphf_batch_config *c);
+int mphf_batch_get_config(const mphf_batch_t *b, mphf_batch_config *c);
+
+/* Times every launch shape on this batch (best of 3 runs after a warm-up),
+ * keeps the fastest, and writes it to *best (may be NULL).  With a non-NULL
+ * cache_path the choice is looked up in / appended to that JSON-lines file,
+ * keyed by key kind, decade of the total key count and SM count.
+ * Synchronous. */
+int mphf_batch_autotune(mphf_batch_t *b, const mphf_request *reqs, uint32_t nreq, void *stream,
+                        const char *cache_path, mphf_batch_config *best);
+
+/* Waits for outstanding runs and releases the executor.  NULL is a no-op. */
+void mphf_batch_free(mphf_batch_t *b);
 
 /* ------------------------------------------------ build without allocating */
 /* Builds the structure of n <= 65536 distinct u64 keys like mphf_build, but

@@ -117,6 +117,9 @@ View make_view(const Header &h, const uint8_t *pilots, const void *remap) {
     return v;
 }
 
+const Header &handle_header(const mphf *m) { return m->hdr; }
+View handle_view(const mphf *m) { return make_view(m->hdr, m->d_pilots, m->d_remap); }
+
 }  // namespace ptrhash
 
 using namespace ptrhash;
@@ -372,8 +375,24 @@ int mphf_query_u64_host(mphf_t *m, const uint64_t *keys_host, uint64_t count, ui
     if (count == 0) return MPHF_OK;
     if (!keys_host || !out_host) { set_error("NULL host buffer"); return MPHF_ERR_ARG; }
     if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
-    std::lock_guard<std::mutex> lock(m->stage_mu);
     cudaStream_t s = (cudaStream_t)stream;
+    // Page-locked host buffers are mapped into the device address space: the
+    // kernel then reads the keys and writes the results across the host link
+    // itself, with no staging copies.
+    cudaPointerAttributes ak, ao;
+    if (cudaPointerGetAttributes(&ak, keys_host) == cudaSuccess && ak.type == cudaMemoryTypeHost &&
+        ak.devicePointer && cudaPointerGetAttributes(&ao, out_host) == cudaSuccess &&
+        ao.type == cudaMemoryTypeHost && ao.devicePointer && ((uintptr_t)ak.devicePointer & 7) == 0 &&
+        ((uintptr_t)ao.devicePointer & 3) == 0) {
+        View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+        int rc = launch_query_u64(m->hdr, v, static_cast<const uint64_t *>(ak.devicePointer), count,
+                                  static_cast<uint32_t *>(ao.devicePointer), false, s);
+        if (rc) return rc;
+        cudaError_t e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "host query: mapped buffers");
+    }
+    cudaGetLastError();   // a pageable pointer is not an error here
+    std::lock_guard<std::mutex> lock(m->stage_mu);
     const uint64_t chunk = 1ull << 24;
     cudaError_t e = cudaSuccess;
     if (m->stage_chunk == 0) {

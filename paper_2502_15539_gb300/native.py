@@ -63,6 +63,19 @@ class mphf_info_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class mphf_request(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_void_p), ("keys_dev", ctypes.c_void_p), ("offsets_dev", ctypes.c_void_p),
+                ("count", ctypes.c_uint64), ("out_dev", ctypes.c_void_p)]
+
+
+class mphf_batch_config(ctypes.Structure):
+    _fields_ = [("keys_per_thread", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # Exported symbols of include/mphf.h with their ctypes signatures.
 _vp, _u64, _i32, _sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
 SIGNATURES = {
@@ -83,6 +96,13 @@ SIGNATURES = {
     "mphf_launch_count": (_u64, []),
     "mphf_build_u64_noalloc": (_i32, [ctypes.POINTER(mphf_params), _vp, _u64, _vp, _sz, ctypes.POINTER(_sz),
                                       _vp]),
+    "mphf_batch_create": (_i32, [ctypes.c_uint32, ctypes.POINTER(_vp)]),
+    "mphf_batch_run": (_i32, [_vp, ctypes.POINTER(mphf_request), ctypes.c_uint32, _vp]),
+    "mphf_batch_set_config": (_i32, [_vp, ctypes.POINTER(mphf_batch_config)]),
+    "mphf_batch_get_config": (_i32, [_vp, ctypes.POINTER(mphf_batch_config)]),
+    "mphf_batch_autotune": (_i32, [_vp, ctypes.POINTER(mphf_request), ctypes.c_uint32, _vp, ctypes.c_char_p,
+                                   ctypes.POINTER(mphf_batch_config)]),
+    "mphf_batch_free": (None, [_vp]),
 }
 
 _lock = threading.Lock()
@@ -276,3 +296,59 @@ def mphf_build_u64_noalloc(keys: torch.Tensor, params: mphf_params | None = None
                                         need.value, ctypes.byref(need), _stream(stream))
     _check(rc, "mphf_build_u64_noalloc")
     return buf.raw[:need.value]
+
+
+# ------------------------------------------------------------------ batches
+def make_requests(items) -> tuple[ctypes.Array, list]:
+    """items: (MPHF, keys tensor, out tensor) or (MPHF, bytes, offsets, out).
+    Returns the C array and the tensors it points to (keep them alive)."""
+    arr = (mphf_request * max(len(items), 1))()
+    keep = []
+    for i, it in enumerate(items):
+        if len(it) == 3:
+            m, keys, out = it
+            arr[i] = mphf_request(m.handle.value, _dev_ptr(keys, torch.int64, "keys") if keys.numel() else None,
+                                  None, keys.numel(), _dev_ptr(out, torch.int32, "out") if out.numel() else None)
+        else:
+            m, data, offsets, out = it
+            arr[i] = mphf_request(m.handle.value, _dev_ptr(data, torch.uint8, "bytes") if data.numel() else None,
+                                  _dev_ptr(offsets, torch.int64, "offsets"), offsets.numel() - 1,
+                                  _dev_ptr(out, torch.int32, "out") if out.numel() else None)
+        keep.append(it)
+    return arr, keep
+
+
+class Batch:
+    """Owns an mphf_batch_t (persistent multi-structure query executor)."""
+
+    def __init__(self, max_requests: int = 1024):
+        self._h = ctypes.c_void_p()
+        _check(load().mphf_batch_create(max_requests, ctypes.byref(self._h)), "mphf_batch_create")
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().mphf_batch_free(h)
+            self._h = None
+
+    def run(self, reqs: ctypes.Array, n: int, stream=None):
+        _check(load().mphf_batch_run(self._h, reqs, n, _stream(stream)), "mphf_batch_run")
+
+    def set_config(self, keys_per_thread=8, threads=256, blocks_per_sm=4, use_graph=True):
+        c = mphf_batch_config(keys_per_thread, threads, blocks_per_sm, int(use_graph))
+        _check(load().mphf_batch_set_config(self._h, ctypes.byref(c)), "mphf_batch_set_config")
+
+    def config(self) -> dict:
+        c = mphf_batch_config()
+        _check(load().mphf_batch_get_config(self._h, ctypes.byref(c)), "mphf_batch_get_config")
+        return c.as_dict()
+
+    def autotune(self, reqs: ctypes.Array, n: int, cache_path: str | None = None, stream=None) -> dict:
+        c = mphf_batch_config()
+        _check(load().mphf_batch_autotune(self._h, reqs, n, _stream(stream),
+                                          cache_path.encode() if cache_path else None, ctypes.byref(c)),
+               "mphf_batch_autotune")
+        return c.as_dict()

@@ -1,0 +1,115 @@
+"""Multi-structure persistent batch kernel against the oracle (bit-exact).
+
+Oracle-built structures of mixed layouts, log-uniform request sizes, 90%
+member and 10% non-member keys; every request's output must equal the
+oracle's one-by-one evaluation, for every launch shape, with and without
+the captured graph, on consecutive runs (both staging sets)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2502_15539_gb300 import workloads as W
+from tests.gpu_common import need_gpu, u32
+
+pytestmark = pytest.mark.gpu
+
+
+def make_set(n_mphf=24, nmax=200_000, qmax=20_000, seed=2):
+    """Structures with n log-uniform in [1e3, nmax] and requests of log-uniform size."""
+    ns = W.log_uniform_int(n_mphf, 1e3, nmax, seed).tolist()
+    qs = W.log_uniform_int(n_mphf, 1, qmax, seed + 1).tolist()
+    structs, reqs = [], []
+    for i, (n, qn) in enumerate(zip(ns, qs)):
+        params = {} if i % 3 else {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC}
+        keys = W.u64_keys(n, seed=100 + i)
+        ref = O.OracleMPHF.build_u64(W.as_uint64_numpy(keys), **params)
+        members = keys[W.uniform_index(qn, n, seed=200 + i)]
+        nm = qn // 10
+        q = torch.cat([members[: qn - nm], W.nonmember_u64_keys(nm, n, seed=100 + i)])
+        structs.append(ref)
+        reqs.append(q)
+    return structs, reqs
+
+
+@pytest.fixture(scope="module")
+def batch_set():
+    need_gpu()
+    return make_set()
+
+
+def run_and_check(N, batch, structs, reqs, extra_bytes=None):
+    ms = [N.mphf_deserialize(r.serialize()) for r in structs]
+    items, outs = [], []
+    for m, q in zip(ms, reqs):
+        out = torch.full((q.numel(),), -1, dtype=torch.int32, device="cuda")
+        items.append((m, q.cuda(), out))
+        outs.append(out)
+    if extra_bytes is not None:
+        ref_b, data, off = extra_bytes
+        mb = N.mphf_deserialize(ref_b.serialize())
+        outb = torch.full((off.numel() - 1,), -1, dtype=torch.int32, device="cuda")
+        items.append((mb, data.cuda(), off.cuda(), outb))
+    arr, keep = N.make_requests(items)
+    batch.run(arr, len(items))
+    torch.cuda.synchronize()
+    for ref, q, out in zip(structs, reqs, outs):
+        assert np.array_equal(u32(out), ref.query_u64(W.as_uint64_numpy(q)))
+    if extra_bytes is not None:
+        assert np.array_equal(u32(outb), ref_b.query_bytes(data.numpy(), off.numpy().astype(np.uint64)))
+    return ms, keep
+
+
+@pytest.mark.parametrize("cfg", [(8, 256, 4, True), (2, 128, 1, True), (16, 512, 2, True), (4, 256, 8, False)])
+def test_batch_matches_oracle(batch_set, cfg):
+    N = need_gpu()
+    structs, reqs = batch_set
+    b = N.Batch(64)
+    b.set_config(*cfg)
+    for _ in range(3):   # consecutive runs use both staging sets
+        run_and_check(N, b, structs, reqs)
+
+
+def test_batch_mixes_u64_and_string_structures(batch_set):
+    N = need_gpu()
+    structs, reqs = batch_set
+    ids = torch.arange(3000)
+    data, off = W.strings(ids, seed=9)
+    ref_b = O.OracleMPHF.build_bytes(data.numpy(), off.numpy().astype(np.uint64))
+    qd, qo = W.strings(torch.cat([ids[W.permutation(3000, 1)], torch.arange(3000, 3300)]), seed=9)
+    b = N.Batch(64)
+    run_and_check(N, b, structs[:8], reqs[:8], extra_bytes=(ref_b, qd, qo))
+
+
+def test_batch_empty_requests_and_capacity(batch_set):
+    N = need_gpu()
+    structs, _ = batch_set
+    m = N.mphf_deserialize(structs[0].serialize())
+    empty = torch.empty(0, dtype=torch.int64, device="cuda")
+    out = torch.empty(0, dtype=torch.int32, device="cuda")
+    b = N.Batch(4)
+    arr, keep = N.make_requests([(m, empty, out)] * 2)
+    b.run(arr, 2)
+    arr, keep = N.make_requests([(m, empty, out)] * 5)
+    with pytest.raises(N.MphfError) as e:
+        b.run(arr, 5)
+    assert e.value.code == N.MPHF_ERR_CAPACITY
+
+
+def test_autotune_picks_a_valid_shape_and_caches_it(batch_set, tmp_path):
+    N = need_gpu()
+    structs, reqs = batch_set
+    ms = [N.mphf_deserialize(r.serialize()) for r in structs]
+    items = [(m, q.cuda(), torch.empty(q.numel(), dtype=torch.int32, device="cuda")) for m, q in zip(ms, reqs)]
+    arr, keep = N.make_requests(items)
+    b = N.Batch(64)
+    cache = tmp_path / "tune.jsonl"
+    best = b.autotune(arr, len(items), str(cache))
+    assert best["keys_per_thread"] in (2, 4, 8, 16) and best["threads"] in (128, 256, 512)
+    assert cache.read_text().count("keys_per_thread") == 1
+    b2 = N.Batch(64)
+    assert b2.autotune(arr, len(items), str(cache)) == best           # read from the cache
+    assert cache.read_text().count("keys_per_thread") == 1
+    run_and_check(N, b2, structs, reqs)

@@ -106,6 +106,17 @@ def test_host_buffer_query_matches_device_query():
     assert np.array_equal(got[40 * n:], want[:12345])
 
 
+def test_host_query_from_pageable_memory():
+    """Pageable host buffers take the staged copy path."""
+    N = need_gpu()
+    n = 300_000
+    ref, blob = oracle_structure(n)
+    m = N.mphf_deserialize(blob)
+    q = W.u64_keys(n, 0)[W.permutation(n, 4)]
+    out = N.mphf_query_u64_host(m, q.clone())
+    assert np.array_equal(out.numpy().view(np.uint32), ref.query_u64(W.as_uint64_numpy(q)))
+
+
 def test_serialize_round_trip_is_byte_exact():
     N = need_gpu()
     for n, params in [(1000, {}), (30_000, {"slots_override": 3001, "alpha": 0.9}),
