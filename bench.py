@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=800)
     ap.add_argument("--batch-mphfs", type=int, default=256)
     ap.add_argument("--query-keys", type=int, default=0,
                     help="query a seeded sample of this many member keys per step instead of all n "
@@ -253,6 +255,8 @@ def run_gpu(args):
     del q, out
     torch.cuda.empty_cache()
     batched = None if args.no_batched else run_batched(args, dev, stream)
+    torch.cuda.empty_cache()
+    serving = None if args.no_serving else run_serving(args, dev)
 
     if rank == 0:
         line = {
@@ -282,6 +286,7 @@ def run_gpu(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -348,6 +353,106 @@ def run_batched(args, dev, stream):
             "per_request_launches": {"queries_per_s": total / (plain_ms / 1e3), "ms_per_batch": plain_ms},
             "speedup": plain_ms / batch_ms, "autotuned": tuned, "outputs_identical": same,
             "build_ms_total": build_ms}
+
+
+def run_serving(args, dev):
+    """Serving: 16 resident structures (8 u64 with n log-uniform in [1e6, 5e8],
+    8 string with n log-uniform in [1e6, 1e8], lengths 16..64), requests of
+    log-uniform size in [1, 1e6] (90% members) on a uniformly chosen structure,
+    HBM budget 60% of the structures' bytes (admission queues).  Capacity is
+    measured with all requests arriving at once; then Poisson arrivals at 10%,
+    50% and 90% of it give p50 / p99 latency (arrival to completion)."""
+    import numpy as np
+    import torch
+    from paper_2502_15539_gb300 import native as N
+    from paper_2502_15539_gb300 import workloads as W
+
+    n_u64 = W.log_uniform_int(8, 1e6, 5e8, seed=4).tolist()
+    n_str = W.log_uniform_int(8, 1e6, 1e8, seed=5).tolist()
+    blobs, kinds, sizes = [], [], []
+    for i, n in enumerate(n_u64):
+        keys = W.u64_keys(n, seed=3000 + i, device=dev)
+        m = N.mphf_build(keys)
+        del keys
+        blobs.append(N.mphf_serialize(m))
+        info = N.mphf_info(m)
+        sizes.append(info["pilot_bytes"] + info["remap_bytes"])
+        kinds.append(("u64", n, 3000 + i))
+        del m
+        torch.cuda.empty_cache()
+    for i, n in enumerate(n_str):
+        data, off = W.strings(torch.arange(n, device=dev), seed=4000 + i)
+        m = N.mphf_build(data, offsets=off)
+        del data, off
+        blobs.append(N.mphf_serialize(m))
+        info = N.mphf_info(m)
+        sizes.append(info["pilot_bytes"] + info["remap_bytes"])
+        kinds.append(("bytes", n, 4000 + i))
+        del m
+        torch.cuda.empty_cache()
+    def serve(budget):
+        srv = N.Server(hbm_budget_bytes=budget, slots=4, max_batch_requests=1024, max_batch_keys=1 << 24)
+        sids = [srv.add(b) for b in blobs]
+        return srv, sids
+
+    budget = int(0.6 * sum(sizes))
+    srv, sids = serve(budget)
+
+    R = args.serve_requests
+    counts = W.log_uniform_int(R, 1, 1e6, seed=6).tolist()
+    which = W.uniform_index(R, 16, seed=7).tolist()
+    reqs, keep = [], []
+    for r, (cnt, k) in enumerate(zip(counts, which)):
+        kind, n, seed = kinds[k]
+        nm = cnt // 10
+        if kind == "u64":
+            q = torch.cat([W.u64_keys_at(W.uniform_index(cnt - nm, n, 9000 + r, device=dev), seed=seed),
+                           W.nonmember_u64_keys(nm, n, seed, device=dev)])
+            out = torch.empty(cnt, dtype=torch.int32, device=dev)
+            reqs.append(N.Server.request(sids[k], q, out))
+            keep.append((q, out))
+        else:
+            ids = torch.cat([W.uniform_index(cnt - nm, n, 9000 + r, device=dev),
+                             n + W.uniform_index(nm, n, 9500 + r, device=dev)])
+            d, o = W.strings(ids, seed=seed)
+            out = torch.empty(cnt, dtype=torch.int32, device=dev)
+            reqs.append(N.Server.request(sids[k], d, out, o))
+            keep.append((d, o, out))
+    torch.cuda.synchronize()
+    total_keys = sum(counts)
+
+    def sweep(srv, seed):
+        # Warm-up, then capacity: everything arrives at t = 0; then Poisson loads.
+        srv.replay(reqs, [0.0] * R)
+        srv.drain()
+        srv.stats(reset=True)
+        srv.replay(reqs, [0.0] * R)
+        srv.drain()
+        burst = srv.stats(reset=True)
+        cap = burst["queries_per_s"]
+        levels = {}
+        rng = np.random.default_rng(seed)
+        for load in (0.1, 0.5, 0.9):
+            rate_req = load * cap / (total_keys / R)          # requests per second
+            arrivals = np.cumsum(rng.exponential(1e6 / rate_req, R))
+            srv.replay(reqs, arrivals)
+            srv.drain()
+            st = srv.stats(reset=True)
+            levels[f"{int(load * 100)}%"] = {k: st[k] for k in ("p50_us", "p99_us", "max_us", "queries_per_s",
+                                                               "mean_requests_per_batch", "evictions", "admissions")}
+        return {"capacity_queries_per_s": cap, "burst_p50_us": burst["p50_us"], "burst_p99_us": burst["p99_us"],
+                "poisson": levels}
+
+    tight = sweep(srv, 8)
+    srv.close()
+    srv, sids_all = serve(2 * sum(sizes))
+    # same requests, structure ids are assigned in the same order
+    roomy = sweep(srv, 9)
+    srv.close()
+    return {"workload": f"16 structures (8 u64, n {min(n_u64)}..{max(n_u64)}; 8 string, n {min(n_str)}..{max(n_str)}, "
+                        f"len 16..64), {R} requests of log-uniform size [1, 1e6] (sum {total_keys}), 4 slots",
+            "budget_60pct": dict(tight, hbm_budget_bytes=budget, structure_bytes=sum(sizes)),
+            "all_resident": roomy}
 
 
 def cpu_baseline(m, q, sample: int):

@@ -236,6 +236,72 @@ int mphf_batch_autotune(mphf_batch_t *b, const mphf_request *reqs, uint32_t nreq
 /* Waits for outstanding runs and releases the executor.  NULL is a no-op. */
 void mphf_batch_free(mphf_batch_t *b);
 
+/* ----------------------------------------------------------- serving */
+/* A serving loop with continuous batching (no paper counterpart; the
+ * paper's streaming query_all of App. A is the single-caller analogue).
+ * Structures are registered as serialized bytes and kept on the device
+ * while their pilot + remap bytes fit hbm_budget_bytes; idle ones (nothing
+ * queued or in flight) are evicted least-recently-used when a structure with
+ * queued requests needs room, and re-admitted later from the host copy.
+ * A dispatcher thread coalesces queued requests of resident structures,
+ * in arrival order, into batches of at most max_batch_requests requests and
+ * max_batch_keys keys, and runs each batch on one of `slots` streams
+ * (persistent batch kernel), so up to `slots` batches overlap on the GPU and
+ * requests that arrive meanwhile join the next free slot. */
+typedef struct {
+    uint64_t hbm_budget_bytes;    /* device bytes for resident structures   */
+    uint32_t max_batch_requests;  /* 1..4096 requests per launch             */
+    uint64_t max_batch_keys;      /* keys per launch (a single larger request
+                                     still runs alone)                        */
+    int32_t  slots;               /* 1..16 concurrent batches (streams)      */
+} mphf_server_config;
+
+typedef struct {
+    uint32_t        structure;    /* id from mphf_server_add                 */
+    const void     *keys_dev;     /* u64 keys, or packed bytes (device)      */
+    const uint64_t *offsets_dev;  /* byte keys: count+1 offsets; else NULL   */
+    uint64_t        count;
+    uint32_t       *out_dev;      /* count uint32_t (device)                 */
+} mphf_server_req;
+
+typedef struct {
+    double   p50_us, p99_us, max_us, mean_us;   /* arrival -> completion   */
+    double   queries_per_s;       /* completed keys / (last completion -
+                                     first arrival)                          */
+    uint64_t requests, queries, batches;
+    double   mean_requests_per_batch;
+    uint64_t admissions, evictions, resident_bytes;
+} mphf_server_stats_t;
+
+typedef struct mphf_server mphf_server_t;
+
+/* Defaults: 16 GiB budget, 1024 requests and 2^24 keys per batch, 4 slots. */
+int mphf_server_default_config(mphf_server_config *c);
+int mphf_server_create(const mphf_server_config *cfg, mphf_server_t **out);
+/* Registers a structure (copied; validated by loading it once).  It is
+ * admitted onto the device when requests for it are queued.  Errors:
+ * MPHF_ERR_FORMAT, MPHF_ERR_CAPACITY (larger than the whole budget). */
+int mphf_server_add(mphf_server_t *s, const void *serialized, size_t len, uint32_t *id);
+/* Unregisters: waits for its queued and in-flight requests, frees it. */
+int mphf_server_remove(mphf_server_t *s, uint32_t id);
+/* Queues one request; the caller's buffers must stay valid until it is done.
+ * Latency is measured from this call. */
+int mphf_server_submit(mphf_server_t *s, const mphf_server_req *r, uint64_t *ticket);
+/* Open-loop load: request i arrives arrival_us[i] microseconds after the
+ * call; the calling thread submits each at its time and its latency is
+ * measured from that scheduled arrival.  Returns after the last submit. */
+int mphf_server_replay(mphf_server_t *s, const mphf_server_req *reqs, const double *arrival_us, uint32_t n,
+                       uint64_t *tickets);
+/* Waits for one request (MPHF_ERR_TIMEOUT after timeout_us); *status gets
+ * the request's own result code. */
+int mphf_server_wait(mphf_server_t *s, uint64_t ticket, uint64_t timeout_us, int *status);
+/* Waits until nothing is queued or in flight. */
+int mphf_server_drain(mphf_server_t *s, uint64_t timeout_us);
+/* Latency percentiles and throughput of completed requests (reset: clear). */
+int mphf_server_stats(mphf_server_t *s, int reset, mphf_server_stats_t *out);
+/* Stops the dispatcher after the queued work, and frees everything. */
+void mphf_server_free(mphf_server_t *s);
+
 /* ------------------------------------------------ build without allocating */
 /* Builds the structure of n <= 65536 distinct u64 keys like mphf_build, but
  * allocates no device memory: all of its device working memory lives in one

@@ -23,6 +23,7 @@ struct mphf {
     uint32_t *d_stage_out[2] = {nullptr, nullptr};
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_q[2] = {}, ev_d2h[2] = {};
+    bool owns_device_memory = true;   // false: pilots / remap live in a caller's arena
 };
 
 namespace ptrhash {
@@ -206,8 +207,10 @@ static void free_handle(mphf_t *m) {
     int dev_prev = 0;
     cudaGetDevice(&dev_prev);
     cudaSetDevice(m->device);
-    cudaFree(m->d_pilots);
-    cudaFree(m->d_remap);
+    if (m->owns_device_memory) {
+        cudaFree(m->d_pilots);
+        cudaFree(m->d_remap);
+    }
     for (int i = 0; i < 2; i++) {
         cudaFree(m->d_stage_keys[i]);
         cudaFree(m->d_stage_out[i]);
@@ -221,11 +224,10 @@ static void free_handle(mphf_t *m) {
     delete m;
 }
 
-int mphf_deserialize(const void *host_buf, size_t len, mphf_t **out) {
-    if (!out) { set_error("out is NULL"); return MPHF_ERR_ARG; }
-    *out = nullptr;
-    if (!host_buf) { set_error("buffer is NULL"); return MPHF_ERR_ARG; }
-    const uint8_t *b = (const uint8_t *)host_buf;
+}  // extern "C"
+
+// Parses and checks a serialized header; *pb gets the pilot byte count.
+static int parse_serialized(const uint8_t *b, size_t len, Header *out, uint64_t *pb_out) {
     if (len < 128 || memcmp(b, kMagic, 8) != 0 || rd32(b + 8) != 1) {
         set_error("not a PtrHash v1 structure");
         return MPHF_ERR_FORMAT;
@@ -256,6 +258,63 @@ int mphf_deserialize(const void *host_buf, size_t len, mphf_t **out) {
         bad = h.remap_bytes != want || len < 128 + round64(pb) + h.remap_bytes;
     }
     if (bad) { set_error("inconsistent header fields"); return MPHF_ERR_FORMAT; }
+    *out = h;
+    *pb_out = pb;
+    return MPHF_OK;
+}
+
+namespace ptrhash {
+
+// Device bytes a serialized structure needs in an arena (256-byte aligned parts).
+int serialized_device_bytes(const void *blob, size_t len, uint64_t *bytes) {
+    Header h;
+    uint64_t pb = 0;
+    int rc = parse_serialized((const uint8_t *)blob, len, &h, &pb);
+    if (rc) return rc;
+    *bytes = ((pb + 255) & ~255ull) + ((h.remap_bytes + 255) & ~255ull);
+    return MPHF_OK;
+}
+
+// A handle whose pilots and remap live at `dev` (caller-owned, at least
+// serialized_device_bytes long); the copies are queued on `s`.
+int handle_in_arena(const void *blob, size_t len, uint8_t *dev, cudaStream_t s, mphf_t **out) {
+    *out = nullptr;
+    Header h;
+    uint64_t pb = 0;
+    const uint8_t *b = (const uint8_t *)blob;
+    int rc = parse_serialized(b, len, &h, &pb);
+    if (rc) return rc;
+    mphf_t *m = new (std::nothrow) mphf_t();
+    if (!m) { set_error("host allocation"); return MPHF_ERR_OOM; }
+    m->hdr = h;
+    m->owns_device_memory = false;
+    cudaGetDevice(&m->device);
+    m->d_pilots = dev;
+    m->d_remap = dev + ((pb + 255) & ~255ull);
+    cudaError_t e = cudaMemcpyAsync(m->d_pilots, b + 128, pb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h.remap_bytes)
+        e = cudaMemcpyAsync(m->d_remap, b + 128 + round64(pb), h.remap_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "arena load: copy");
+    }
+    *out = m;
+    return MPHF_OK;
+}
+
+}  // namespace ptrhash
+
+extern "C" {
+
+int mphf_deserialize(const void *host_buf, size_t len, mphf_t **out) {
+    if (!out) { set_error("out is NULL"); return MPHF_ERR_ARG; }
+    *out = nullptr;
+    if (!host_buf) { set_error("buffer is NULL"); return MPHF_ERR_ARG; }
+    const uint8_t *b = (const uint8_t *)host_buf;
+    Header h;
+    uint64_t pb = 0;
+    int rc = parse_serialized(b, len, &h, &pb);
+    if (rc) return rc;
     mphf_t *m = new (std::nothrow) mphf_t();
     if (!m) { set_error("host allocation"); return MPHF_ERR_OOM; }
     m->hdr = h;
@@ -266,7 +325,7 @@ int mphf_deserialize(const void *host_buf, size_t len, mphf_t **out) {
     if (e == cudaSuccess && h.remap_bytes)
         e = cudaMemcpy(m->d_remap, b + 128 + round64(pb), h.remap_bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        int rc = cuda_fail(e, "deserialize: device allocation or copy");
+        rc = cuda_fail(e, "deserialize: device allocation or copy");
         free_handle(m);
         return rc;
     }

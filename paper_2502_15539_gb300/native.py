@@ -76,6 +76,27 @@ class mphf_batch_config(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class mphf_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch_requests", ctypes.c_uint32),
+                ("max_batch_keys", ctypes.c_uint64), ("slots", ctypes.c_int32)]
+
+
+class mphf_server_req(ctypes.Structure):
+    _fields_ = [("structure", ctypes.c_uint32), ("keys_dev", ctypes.c_void_p), ("offsets_dev", ctypes.c_void_p),
+                ("count", ctypes.c_uint64), ("out_dev", ctypes.c_void_p)]
+
+
+class mphf_server_stats_t(ctypes.Structure):
+    _fields_ = [("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("queries_per_s", ctypes.c_double), ("requests", ctypes.c_uint64),
+                ("queries", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("mean_requests_per_batch", ctypes.c_double), ("admissions", ctypes.c_uint64),
+                ("evictions", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # Exported symbols of include/mphf.h with their ctypes signatures.
 _vp, _u64, _i32, _sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
 SIGNATURES = {
@@ -103,6 +124,17 @@ SIGNATURES = {
     "mphf_batch_autotune": (_i32, [_vp, ctypes.POINTER(mphf_request), ctypes.c_uint32, _vp, ctypes.c_char_p,
                                    ctypes.POINTER(mphf_batch_config)]),
     "mphf_batch_free": (None, [_vp]),
+    "mphf_server_default_config": (_i32, [ctypes.POINTER(mphf_server_config)]),
+    "mphf_server_create": (_i32, [ctypes.POINTER(mphf_server_config), ctypes.POINTER(_vp)]),
+    "mphf_server_add": (_i32, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_uint32)]),
+    "mphf_server_remove": (_i32, [_vp, ctypes.c_uint32]),
+    "mphf_server_submit": (_i32, [_vp, ctypes.POINTER(mphf_server_req), ctypes.POINTER(_u64)]),
+    "mphf_server_replay": (_i32, [_vp, ctypes.POINTER(mphf_server_req), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.c_uint32, ctypes.POINTER(_u64)]),
+    "mphf_server_wait": (_i32, [_vp, _u64, _u64, ctypes.POINTER(ctypes.c_int)]),
+    "mphf_server_drain": (_i32, [_vp, _u64]),
+    "mphf_server_stats": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(mphf_server_stats_t)]),
+    "mphf_server_free": (None, [_vp]),
 }
 
 _lock = threading.Lock()
@@ -352,3 +384,75 @@ class Batch:
                                           cache_path.encode() if cache_path else None, ctypes.byref(c)),
                "mphf_batch_autotune")
         return c.as_dict()
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Owns an mphf_server_t (continuous-batching serving loop)."""
+
+    def __init__(self, hbm_budget_bytes: int | None = None, max_batch_requests: int | None = None,
+                 max_batch_keys: int | None = None, slots: int | None = None):
+        lib = load()
+        c = mphf_server_config()
+        _check(lib.mphf_server_default_config(ctypes.byref(c)), "mphf_server_default_config")
+        if hbm_budget_bytes is not None:
+            c.hbm_budget_bytes = hbm_budget_bytes
+        if max_batch_requests is not None:
+            c.max_batch_requests = max_batch_requests
+        if max_batch_keys is not None:
+            c.max_batch_keys = max_batch_keys
+        if slots is not None:
+            c.slots = slots
+        self._h = ctypes.c_void_p()
+        _check(lib.mphf_server_create(ctypes.byref(c), ctypes.byref(self._h)), "mphf_server_create")
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().mphf_server_free(h)
+            self._h = None
+
+    def add(self, blob: bytes) -> int:
+        sid = ctypes.c_uint32()
+        _check(load().mphf_server_add(self._h, blob, len(blob), ctypes.byref(sid)), "mphf_server_add")
+        return sid.value
+
+    def remove(self, sid: int):
+        _check(load().mphf_server_remove(self._h, sid), "mphf_server_remove")
+
+    @staticmethod
+    def request(sid: int, keys: torch.Tensor, out: torch.Tensor, offsets: torch.Tensor | None = None):
+        if offsets is None:
+            return mphf_server_req(sid, keys.data_ptr() if keys.numel() else None, None, keys.numel(),
+                                   out.data_ptr() if out.numel() else None)
+        return mphf_server_req(sid, keys.data_ptr() if keys.numel() else None, offsets.data_ptr(),
+                               offsets.numel() - 1, out.data_ptr() if out.numel() else None)
+
+    def submit(self, req: mphf_server_req) -> int:
+        t = ctypes.c_uint64()
+        _check(load().mphf_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "mphf_server_submit")
+        return t.value
+
+    def replay(self, reqs: list, arrival_us) -> list:
+        n = len(reqs)
+        arr = (mphf_server_req * max(n, 1))(*reqs)
+        at = (ctypes.c_double * max(n, 1))(*[float(x) for x in arrival_us])
+        tk = (ctypes.c_uint64 * max(n, 1))()
+        _check(load().mphf_server_replay(self._h, arr, at, n, tk), "mphf_server_replay")
+        return list(tk)[:n]
+
+    def wait(self, ticket: int, timeout_us: int = 10_000_000) -> int:
+        st = ctypes.c_int()
+        _check(load().mphf_server_wait(self._h, ticket, timeout_us, ctypes.byref(st)), "mphf_server_wait")
+        return st.value
+
+    def drain(self, timeout_us: int = 60_000_000):
+        _check(load().mphf_server_drain(self._h, timeout_us), "mphf_server_drain")
+
+    def stats(self, reset: bool = False) -> dict:
+        st = mphf_server_stats_t()
+        _check(load().mphf_server_stats(self._h, int(reset), ctypes.byref(st)), "mphf_server_stats")
+        return st.as_dict()
