@@ -28,7 +28,7 @@ namespace ptrhash {
 constexpr int kSearchThreads = 256;
 constexpr int kMaxBucket = 2048;        // larger buckets fail the part
 constexpr int kSmallBucket = 16;        // pilot-parallel search up to this size
-constexpr int kPendingCap = 4096;       // evicted buckets waiting for a pilot
+constexpr int kPendingCap = 8192;       // deferred or evicted buckets waiting for a pilot
 constexpr int kSetSize = 4096;          // slot set for self-collision checks
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kMaxSlots = 1ull << 20;   // bitvector in shared memory
@@ -74,7 +74,8 @@ struct SearchArgs {
     uint8_t *pilots;
     uint32_t *taken;          // linear bitmap of P*S bits (zeroed)
     uint32_t *owner_scratch;  // gridDim.x * S
-    uint32_t *order_scratch;  // gridDim.x * B
+    uint64_t *order_scratch;  // gridDim.x * B packed descriptors (bucket | size | key offset)
+    uint64_t *ohash_scratch;  // gridDim.x * S hashes in processing order
     uint32_t *status;         // per part
     unsigned long long *evictions;
     uint32_t *next_part;
@@ -90,13 +91,27 @@ __device__ __forceinline__ uint32_t slot_in_part(const SearchArgs &a, uint64_t x
 __device__ __forceinline__ bool bit_of(const uint32_t *bits, uint32_t s) { return (bits[s >> 5] >> (s & 31)) & 1u; }
 
 struct SearchShared {
-    uint32_t *bits;     // S bits
-    uint32_t *hist;     // kMaxBucket + 1
+    uint32_t *bits;     // S bits; during preparation, per-warp size counters
+    uint32_t *hist;     // kMaxBucket + 1: first processing position of each size
     uint64_t *hcache;   // kMaxBucket hashes of the current bucket
-    uint32_t *set;      // kSetSize slot-set entries (generation << 21 | slot)
-    uint32_t *pending;  // kPendingCap
+    uint32_t *set;      // kSetSize slot-set entries (generation << 21 | slot);
+                        // during preparation, first key offset of each size
+    uint32_t *pend;     // kPendingCap waiting buckets (bucket | size << 20)
+    uint32_t *np;       // how many
     uint32_t *recent;   // 16
 };
+
+constexpr int kSearchWarps = kSearchThreads / 32;
+// Slot owner entries and waiting buckets pack bucket | size << 20.
+constexpr uint32_t kOwnerShift = 20, kOwnerMask = (1u << 20) - 1;
+__device__ __forceinline__ uint32_t pack_owner(uint32_t b, uint32_t z) { return b | (z << kOwnerShift); }
+constexpr uint64_t kPrepWords = (uint64_t)kSearchWarps * (kMaxBucket + 1);   // per-warp size counters
+
+// Processing-order descriptor: bucket (32 bits) | size (12 bits) | offset of
+// its first hash in the ordered hash array (20 bits; a part has <= 2^20 keys).
+__device__ __forceinline__ uint64_t pack_desc(uint64_t b, uint64_t z, uint64_t koff) {
+    return b | (z << 32) | (koff << 44);
+}
 
 // Inserts slot s for generation gen; false if it is already in the set.
 __device__ __forceinline__ bool set_insert(uint32_t *set, uint32_t s, uint32_t gen) {
@@ -200,9 +215,9 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
                 if (j < s) {
                     sl[j] = slot_in_part<REDUCE>(a, hj ^ hp);
                     if (bit_of(sh.bits, sl[j])) {
-                        const uint32_t o = owner[sl[j]];
-                        if (use_tabu && in_recent(sh.recent, o)) ok = false;
-                        const uint64_t z = bucket_size(a, gb0, o);
+                        const uint32_t oe = owner[sl[j]];
+                        if (use_tabu && in_recent(sh.recent, oe & kOwnerMask)) ok = false;
+                        const uint64_t z = oe >> kOwnerShift;
                         cost += z * z;
                     }
                 }
@@ -232,9 +247,9 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
             const uint32_t sl = slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp);
             if (!set_insert(sh.set, sl, gen)) bad = true;
             else if (bit_of(sh.bits, sl)) {
-                const uint32_t o = owner[sl];
-                if (use_tabu && in_recent(sh.recent, o)) bad = true;
-                const uint64_t z = bucket_size(a, gb0, o);
+                const uint32_t oe = owner[sl];
+                if (use_tabu && in_recent(sh.recent, oe & kOwnerMask)) bad = true;
+                const uint64_t z = oe >> kOwnerShift;
                 cost += z * z;
             }
         }
@@ -245,48 +260,78 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
     return best_p;
 }
 
-// Greedy + hash-evict placement of one part by one warp.  Returns a status.
+// Greedy + hash-evict placement by one warp, over stream positions
+// [first, last) and the waiting buckets in shared memory (deferred or
+// evicted, largest first; ties go to the waiting bucket).  The hashes of
+// the next bucket of the stream are requested while the current one is
+// searched.  Returns a status.
 template <int REDUCE>
-__device__ uint32_t search_part(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint32_t *order,
-                                uint32_t nb, uint64_t p, int lane, unsigned long long &evicted) {
+__device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint64_t *order,
+                                  const uint64_t *ohash, uint32_t first, uint32_t last, uint64_t p, int lane,
+                                  unsigned long long &evicted) {
     const uint64_t gb0 = p * a.B;
-    uint32_t next = 0, np = 0, rpos = 0, gen = 0;
+    uint32_t next = first, np = *sh.np, rpos = 0, gen = 0;
+    if (np > (uint32_t)kPendingCap) return kPartPendingFull;
+    uint32_t wbase = kNone;          // first position held in the descriptor window
+    uint64_t wdesc = 0;              // lane l: descriptor of position wbase + l
+    uint32_t pf_pos = kNone;         // position whose hashes were prefetched
+    uint64_t pf_h = 0;
     for (int i = lane; i < 16; i += 32) sh.recent[i] = kNone;
     for (int i = lane; i < kSetSize; i += 32) sh.set[i] = 0;
     __syncwarp();
+    uint32_t status = kPartOk;
     for (;;) {
-        // The largest waiting bucket: next in the size order, or an evicted one.
-        uint64_t best_sz = 0;
-        uint32_t best_i = kNone;
+        if (next < last && (wbase == kNone || next >= wbase + 32)) {
+            wbase = next;
+            wdesc = next + lane < last ? order[next + lane] : 0;
+        }
+        const uint64_t od = next < last ? __shfl_sync(0xFFFFFFFFu, wdesc, (next - wbase) & 31) : 0;
+        const uint32_t ord_z = (uint32_t)(od >> 32) & 0xFFFu;
+        uint32_t best_z = 0, best_i = kNone;
         for (uint32_t i = lane; i < np; i += 32) {
-            const uint64_t z = bucket_size(a, gb0, sh.pending[i]);
-            if (z > best_sz || (z == best_sz && i < best_i)) { best_sz = z; best_i = i; }
+            const uint32_t z = sh.pend[i] >> kOwnerShift;
+            if (z > best_z || (z == best_z && i < best_i)) { best_z = z; best_i = i; }
         }
         for (int off = 16; off; off >>= 1) {
-            const uint64_t oz = __shfl_xor_sync(0xFFFFFFFFu, best_sz, off);
+            const uint32_t oz = __shfl_xor_sync(0xFFFFFFFFu, best_z, off);
             const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, best_i, off);
-            if (oz > best_sz || (oz == best_sz && oi < best_i)) { best_sz = oz; best_i = oi; }
+            if (oz > best_z || (oz == best_z && oi < best_i)) { best_z = oz; best_i = oi; }
         }
-        const uint32_t ord_b = next < nb ? order[next] : kNone;
-        const uint64_t ord_sz = ord_b != kNone ? bucket_size(a, gb0, ord_b) : 0;
-        if (ord_b == kNone && np == 0) return kPartOk;
+        if (next >= last && np == 0) break;
         uint32_t b;
-        if (np > 0 && best_sz >= ord_sz) {   // ties: the evicted bucket goes first
-            b = sh.pending[best_i];
+        int s;
+        uint64_t myh;
+        if (np > 0 && best_z >= ord_z) {
+            b = sh.pend[best_i] & kOwnerMask;
+            s = (int)best_z;
             __syncwarp();
-            if (lane == 0) sh.pending[best_i] = sh.pending[np - 1];
+            if (lane == 0) sh.pend[best_i] = sh.pend[np - 1];
             np--;
             __syncwarp();
+            const uint64_t kbase = a.bstart[gb0 + b];
+            myh = lane < s ? a.sorted[kbase + lane] : 0;
+            if (s > kSmallBucket) {
+                for (int j = lane; j < s; j += 32) sh.hcache[j] = a.sorted[kbase + j];
+                __syncwarp();
+            }
         } else {
-            b = ord_b;
+            b = (uint32_t)od;
+            s = (int)ord_z;
+            const uint64_t koff = od >> 44;
+            myh = (pf_pos == next) ? pf_h : (lane < s ? ohash[koff + lane] : 0);
+            if (s > kSmallBucket) {
+                for (int j = lane; j < s; j += 32) sh.hcache[j] = ohash[koff + j];
+                __syncwarp();
+            }
             next++;
         }
-        const int s = (int)bucket_size(a, gb0, b);
-        const uint64_t kbase = a.bstart[gb0 + b];
-        uint64_t myh = lane < s ? a.sorted[kbase + lane] : 0;
-        if (s > kSmallBucket) {
-            for (int j = lane; j < s; j += 32) sh.hcache[j] = a.sorted[kbase + j];
-            __syncwarp();
+        if (next < last && wbase != kNone && next < wbase + 32) {
+            const uint64_t d2 = __shfl_sync(0xFFFFFFFFu, wdesc, (next - wbase) & 31);
+            const uint32_t z2 = (uint32_t)(d2 >> 32) & 0xFFFu;
+            pf_pos = next;
+            pf_h = (z2 <= (uint32_t)kSmallBucket && (uint32_t)lane < z2) ? ohash[(d2 >> 44) + lane] : 0;
+        } else {
+            pf_pos = kNone;
         }
         int chosen = s <= kSmallBucket ? greedy_small<REDUCE>(a, sh.bits, myh, s, lane)
                                        : greedy_large<REDUCE>(a, sh, s, gen, lane);
@@ -295,34 +340,36 @@ __device__ uint32_t search_part(const SearchArgs &a, const SearchShared &sh, uin
             // The tabu only breaks eviction cycles: when it blocks every pilot
             // that does not self-collide, it is ignored for this bucket.
             if (chosen < 0) chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, false);
-            if (chosen < 0) return kPartNoPilot;
+            if (chosen < 0) { status = kPartNoPilot; break; }
             const uint64_t hp = a.C * ((uint64_t)chosen ^ a.seed);
             for (int j = 0; j < s; j++) {
                 const uint64_t hj = s <= kSmallBucket ? __shfl_sync(0xFFFFFFFFu, myh, j) : sh.hcache[j];
                 const uint32_t sl = slot_in_part<REDUCE>(a, hj ^ hp);
                 if (!bit_of(sh.bits, sl)) continue;        // free, or its owner already evicted
-                const uint32_t o = owner[sl];
+                const uint32_t oe = owner[sl];
+                const uint32_t o = oe & kOwnerMask;
+                const uint64_t os = oe >> kOwnerShift;
                 const uint64_t ob = a.bstart[gb0 + o];
-                const uint64_t os = bucket_size(a, gb0, o);
                 const uint64_t ohp = a.C * ((uint64_t)a.pilots[gb0 + o] ^ a.seed);
                 for (uint64_t k = lane; k < os; k += 32) {
                     const uint32_t osl = slot_in_part<REDUCE>(a, a.sorted[ob + k] ^ ohp);
                     atomicAnd(&sh.bits[osl >> 5], ~(1u << (osl & 31)));
                 }
-                if (np >= (uint32_t)kPendingCap) return kPartPendingFull;
-                if (lane == 0) sh.pending[np] = o;
+                if (np >= (uint32_t)kPendingCap) { status = kPartPendingFull; break; }
+                if (lane == 0) sh.pend[np] = oe;
                 np++;
                 evicted++;
                 __syncwarp();
             }
-            if (evicted > a.evict_cap) return kPartEvictCap;
+            if (status != kPartOk) break;
+            if (evicted > a.evict_cap) { status = kPartEvictCap; break; }
         }
         const uint64_t hp = a.C * ((uint64_t)chosen ^ a.seed);
         for (int j = lane; j < s; j += 32) {
             const uint64_t hj = s <= kSmallBucket ? myh : sh.hcache[j];
             const uint32_t sl = slot_in_part<REDUCE>(a, hj ^ hp);
             atomicOr(&sh.bits[sl >> 5], 1u << (sl & 31));
-            owner[sl] = b;
+            owner[sl] = pack_owner(b, (uint32_t)s);
         }
         if (lane == 0) {
             a.pilots[gb0 + b] = (uint8_t)chosen;
@@ -331,36 +378,149 @@ __device__ uint32_t search_part(const SearchArgs &a, const SearchShared &sh, uin
         rpos = (rpos + 1) & 15;
         __syncwarp();
     }
+    __syncwarp();
+    if (lane == 0) *sh.np = np;
+    __syncwarp();
+    return status;
+}
+
+// Greedy placement of small buckets (<= kSmallBucket keys) by every warp,
+// in deterministic rounds.  In a round each warp with a bucket finds its
+// smallest free pilot on the same snapshot of the bitvector; then a warp
+// commits its slots only if no earlier warp of the round picked any of
+// them (the others retry in the next round on the updated bitvector).
+// Buckets with no free pilot at all are placed by hash-evict (warp 0,
+// serially, with their cascade) before the next round.  Finished warps take
+// the next buckets of the stream in warp order, so the outcome depends only
+// on the input.
+struct RoundShared {
+    uint32_t slots[kSearchWarps][kSmallBucket];
+    int32_t chosen[kSearchWarps];     // pilot, -1: none found, -2: no bucket
+    uint32_t size[kSearchWarps];
+    uint32_t pos[kSearchWarps];       // stream position of the warp's bucket
+    uint32_t done[kSearchWarps];      // committed or deferred this round
+    uint32_t cursor;
+};
+
+template <int REDUCE>
+__device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint64_t *order,
+                                  const uint64_t *ohash, uint32_t first, uint32_t last, uint64_t p, int lane,
+                                  unsigned long long &evicted);
+
+template <int REDUCE>
+__device__ void greedy_rounds(const SearchArgs &a, const SearchShared &sh, RoundShared &rs, uint32_t *owner,
+                              const uint64_t *order, const uint64_t *ohash, uint32_t first, uint32_t last,
+                              uint64_t p, int warp, int lane, unsigned long long &evicted, uint32_t *status) {
+    const uint64_t gb0 = p * a.B;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < kSearchWarps; w++) rs.pos[w] = first + w < last ? first + w : kNone;
+        rs.cursor = first + kSearchWarps < last ? first + kSearchWarps : last;
+    }
+    __syncthreads();
+    for (;;) {
+        const uint32_t pos = rs.pos[warp];
+        uint32_t b = 0, z = 0;
+        int chosen = -2;
+        uint32_t my_sl = 0;
+        if (pos != kNone) {
+            const uint64_t d = order[pos];
+            b = (uint32_t)d;
+            z = (uint32_t)(d >> 32) & 0xFFFu;
+            const uint64_t myh = lane < (int)z ? ohash[(d >> 44) + lane] : 0;
+            chosen = greedy_small<REDUCE>(a, sh.bits, myh, (int)z, lane);
+            if (chosen >= 0 && lane < (int)z) {
+                my_sl = slot_in_part<REDUCE>(a, myh ^ (a.C * ((uint64_t)chosen ^ a.seed)));
+                rs.slots[warp][lane] = my_sl;
+            }
+        }
+        if (lane == 0) { rs.chosen[warp] = chosen; rs.size[warp] = z; }
+        __syncthreads();
+        // No warp has a bucket left: the phase is over.
+        bool any = false;
+        for (int w = 0; w < kSearchWarps; w++) any |= rs.chosen[w] != -2;
+        if (!any) break;
+        uint32_t done = 0;
+        if (chosen >= 0) {
+            bool clash = false;
+            if (lane < (int)z)
+                for (int w = 0; w < warp; w++) {
+                    if (rs.chosen[w] < 0) continue;
+                    for (uint32_t j = 0; j < rs.size[w]; j++) clash |= rs.slots[w][j] == my_sl;
+                }
+            if (!__any_sync(0xFFFFFFFFu, clash)) {
+                if (lane < (int)z) {
+                    atomicOr(&sh.bits[my_sl >> 5], 1u << (my_sl & 31));
+                    owner[my_sl] = pack_owner(b, z);
+                }
+                if (lane == 0) a.pilots[gb0 + b] = (uint8_t)chosen;
+                done = 1;
+            }
+        } else if (chosen == -1) {
+            done = 1;   // deferred below, in warp order
+        }
+        if (lane == 0) rs.done[warp] = done;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 0; w < kSearchWarps; w++) {
+                if (!rs.done[w]) continue;
+                if (rs.chosen[w] == -1) {
+                    const uint32_t i = (*sh.np)++;
+                    if (i < (uint32_t)kPendingCap) sh.pend[i] = pack_owner((uint32_t)order[rs.pos[w]], rs.size[w]);
+                }
+                rs.pos[w] = rs.cursor < last ? rs.cursor++ : kNone;
+            }
+        }
+        __syncthreads();
+        // A bucket without a free pilot is placed now, by hash-evict, with
+        // the whole cascade of evicted buckets, before the next round.
+        if (*sh.np > 0) {
+            if (warp == 0) {
+                const uint32_t st = search_serial<REDUCE>(a, sh, owner, order, ohash, 0, 0, p, lane, evicted);
+                if (lane == 0 && st != kPartOk) *status = st;
+            }
+            __syncthreads();
+            if (*status != kPartOk) break;
+        }
+    }
+    __syncthreads();
 }
 
 template <int REDUCE>
 __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint64_t words = (a.S + 31) / 32;
+    const uint64_t bits_words = words > kPrepWords ? words : kPrepWords;
     SearchShared sh;
     sh.hcache = reinterpret_cast<uint64_t *>(smem);
     sh.bits = reinterpret_cast<uint32_t *>(sh.hcache + kMaxBucket);
-    sh.hist = sh.bits + words;
+    sh.hist = sh.bits + bits_words;
     sh.set = sh.hist + (kMaxBucket + 1);
-    sh.pending = sh.set + kSetSize;
-    sh.recent = sh.pending + kPendingCap;
-    __shared__ uint32_t s_part, s_flag, s_nb, s_status;
+    sh.pend = sh.set + kSetSize;
+    sh.recent = sh.pend + kPendingCap;
+    __shared__ uint32_t s_part, s_flag, s_nb, s_status, s_np;
+    __shared__ RoundShared rs;
+    sh.np = &s_np;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *owner = a.owner_scratch + (uint64_t)blockIdx.x * a.S;
-    uint32_t *order = a.order_scratch + (uint64_t)blockIdx.x * a.B;
+    uint64_t *order = a.order_scratch + (uint64_t)blockIdx.x * a.B;
+    uint64_t *ohash = a.ohash_scratch + (uint64_t)blockIdx.x * a.S;
+    uint32_t *cnt = sh.bits;      // [kSearchWarps][kMaxBucket + 1] during preparation
+    uint32_t *kbase = sh.set;     // [kMaxBucket + 1] during preparation
+    const uint64_t chunk = (a.B + kSearchWarps - 1) / kSearchWarps;
     for (;;) {
         if (tid == 0) { s_part = atomicAdd(a.next_part, 1u); s_flag = 0; }
         __syncthreads();
         const uint64_t p = s_part;
         if (p >= a.P) break;
         const uint64_t gb0 = p * a.B;
-        for (uint64_t w = tid; w < words; w += blockDim.x) sh.bits[w] = 0;
-        for (int z = tid; z <= kMaxBucket; z += blockDim.x) sh.hist[z] = 0;
+        // 1. Bucket sizes, counted per warp over its own range of buckets.
+        for (uint64_t w = tid; w < kPrepWords; w += blockDim.x) cnt[w] = 0;
         __syncthreads();
-        for (uint64_t b = tid; b < a.B; b += blockDim.x) {
+        const uint64_t lo = warp * chunk, hi = (lo + chunk < a.B ? lo + chunk : a.B);
+        for (uint64_t b = lo + lane; b < hi; b += 32) {
             const uint32_t z = a.bstart[gb0 + b + 1] - a.bstart[gb0 + b];
             if (z > (uint32_t)kMaxBucket) s_flag = 1;
-            else if (z) atomicAdd(&sh.hist[z], 1u);
+            else if (z) atomicAdd(&cnt[warp * (kMaxBucket + 1) + z], 1u);
         }
         __syncthreads();
         if (s_flag) {
@@ -368,35 +528,82 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchA
             __syncthreads();
             continue;
         }
-        if (tid == 0) {   // exclusive offsets in order of decreasing size
-            uint32_t run = 0;
-            for (int z = kMaxBucket; z >= 1; z--) { const uint32_t c = sh.hist[z]; sh.hist[z] = run; run += c; }
-            s_nb = run;
+        // 2. Processing order: sizes decreasing; inside a size, warp ranges in
+        //    order.  Position and first key offset of every (size, warp).
+        if (warp == 0) {
+            uint32_t carry_pos = 0, carry_keys = 0;
+            for (int c = 0; c * 32 < kMaxBucket; c++) {
+                const int z = kMaxBucket - 32 * c - lane;   // >= 1 for every chunk and lane
+                uint32_t tot = 0;
+                for (int w = 0; w < kSearchWarps; w++) tot += cnt[w * (kMaxBucket + 1) + z];
+                uint32_t keys = tot * (uint32_t)z, ip = tot, ik = keys;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t tp = __shfl_up_sync(0xFFFFFFFFu, ip, off);
+                    const uint32_t tk = __shfl_up_sync(0xFFFFFFFFu, ik, off);
+                    if (lane >= off) { ip += tp; ik += tk; }
+                }
+                const uint32_t pos0 = carry_pos + ip - tot, key0 = carry_keys + ik - keys;
+                sh.hist[z] = pos0;
+                kbase[z] = key0;
+                uint32_t run = pos0;
+                for (int w = 0; w < kSearchWarps; w++) {
+                    const uint32_t cw = cnt[w * (kMaxBucket + 1) + z];
+                    cnt[w * (kMaxBucket + 1) + z] = run;
+                    run += cw;
+                }
+                carry_pos += __shfl_sync(0xFFFFFFFFu, ip, 31);
+                carry_keys += __shfl_sync(0xFFFFFFFFu, ik, 31);
+            }
+            if (lane == 0) s_nb = carry_pos;
         }
         __syncthreads();
+        // 3. Stable scatter of the descriptors, every warp over its range.
+        for (uint64_t base = lo; base < hi; base += 32) {
+            const uint64_t b = base + lane;
+            const uint32_t z = b < hi ? a.bstart[gb0 + b + 1] - a.bstart[gb0 + b] : 0;
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, z);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1));
+            uint32_t pos = 0;
+            if (z) pos = cnt[warp * (kMaxBucket + 1) + z] + rank;
+            __syncwarp();
+            if (z) {
+                order[pos] = pack_desc(b, z, kbase[z] + (uint64_t)(pos - sh.hist[z]) * z);
+                if (rank == 0) cnt[warp * (kMaxBucket + 1) + z] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // 4. The part's hashes in processing order.
+        const uint32_t nb = s_nb;
+        for (uint32_t pos = tid; pos < nb; pos += blockDim.x) {
+            const uint64_t d = order[pos];
+            const uint32_t b = (uint32_t)d, z = (uint32_t)(d >> 32) & 0xFFFu;
+            const uint64_t koff = d >> 44, src = a.bstart[gb0 + b];
+            for (uint32_t k = 0; k < z; k++) ohash[koff + k] = a.sorted[src + k];
+        }
+        const uint32_t n_large = sh.hist[kSmallBucket];   // positions of buckets > kSmallBucket keys
+        for (uint64_t w = tid; w < bits_words; w += blockDim.x) sh.bits[w] = 0;
+        if (tid == 0) { s_np = 0; s_status = kPartOk; }
+        __syncthreads();
+        // Phase 1: the large buckets, serially, with hash-evict.
+        unsigned long long ev = 0;
         if (warp == 0) {
-            // Stable scatter: same-size buckets keep increasing bucket order.
-            for (uint64_t base = 0; base < a.B; base += 32) {
-                const uint64_t b = base + lane;
-                const uint32_t z = b < a.B ? a.bstart[gb0 + b + 1] - a.bstart[gb0 + b] : 0;
-                const unsigned peers = __match_any_sync(0xFFFFFFFFu, z);
-                const unsigned rank = __popc(peers & ((1u << lane) - 1));
-                uint32_t pos = 0;
-                if (z) pos = sh.hist[z] + rank;
-                __syncwarp();
-                if (z) {
-                    order[pos] = (uint32_t)b;
-                    if (rank == 0) sh.hist[z] += __popc(peers);
-                }
-                __syncwarp();
-            }
-            unsigned long long ev = 0;
-            const uint32_t st = search_part<REDUCE>(a, sh, owner, order, s_nb, p, lane, ev);
-            if (lane == 0) {
-                a.status[p] = st;
-                atomicAdd(a.evictions, ev);
-                s_status = st;
-            }
+            const uint32_t st = search_serial<REDUCE>(a, sh, owner, order, ohash, 0, n_large, p, lane, ev);
+            if (lane == 0) s_status = st;
+        }
+        __syncthreads();
+        // Phase 2: the small buckets, every warp, greedy; failures wait.
+        if (s_status == kPartOk)
+            greedy_rounds<REDUCE>(a, sh, rs, owner, order, ohash, n_large, nb, p, warp, lane, ev, &s_status);
+        __syncthreads();
+        // Phase 3: what waits, serially, with hash-evict.
+        if (warp == 0 && s_status == kPartOk) {
+            const uint32_t st = search_serial<REDUCE>(a, sh, owner, order, ohash, nb, nb, p, lane, ev);
+            if (lane == 0) s_status = st;
+        }
+        if (warp == 0 && lane == 0) {
+            a.status[p] = s_status;
+            atomicAdd(a.evictions, ev);
         }
         __syncthreads();
         if (s_status == kPartOk) {   // publish the part's slots into the global bitmap
@@ -497,6 +704,13 @@ struct DevBuf {
     void *release() { void *q = p; p = nullptr; return q; }
 };
 
+// Dynamic shared memory of pilot_search_kernel for S slots per part.
+static size_t search_smem_bytes(uint64_t S) {
+    const uint64_t words = (S + 31) / 32;
+    const uint64_t bits_words = words > kPrepWords ? words : kPrepWords;
+    return kMaxBucket * 8 + bits_words * 4 + (kMaxBucket + 1) * 4 + kSetSize * 4 + kPendingCap * 4 + 16 * 4;
+}
+
 static unsigned grid_for(uint64_t work, int sms) {
     const uint64_t want = (work + 255) / 256;
     const uint64_t cap = (uint64_t)sms * 32;
@@ -522,6 +736,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     int rc = choose_layout(n, prm.lambda, prm.alpha, prm.slots_override, &P, &S, &B, &reduce);
     if (rc) return rc;
     if (S > kMaxSlots) { set_error("S=%llu above the %llu slots a part can hold", (unsigned long long)S, (unsigned long long)kMaxSlots); return MPHF_ERR_CAPACITY; }
+    if (B > kOwnerMask) { set_error("B=%llu buckets per part: lambda too small", (unsigned long long)B); return MPHF_ERR_ARG; }
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -533,14 +748,15 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
 
     const uint64_t total = P * S, nbkt = P * B, words = (total + 31) / 32;
     const unsigned search_grid = (unsigned)(P < (uint64_t)sms ? P : (uint64_t)sms);
-    DevBuf hash, sorted, bstart, pilots, taken, owner, order, status, flags, cub_tmp;
+    DevBuf hash, sorted, bstart, pilots, taken, owner, order, ohash, status, flags, cub_tmp;
     CK(hash.alloc(n * 8));
     CK(sorted.alloc(n * 8));
     CK(bstart.alloc((nbkt + 1) * 4));
     CK(pilots.alloc((nbkt + 63) & ~63ull));
     CK(taken.alloc((words + 1) * 4));
     CK(owner.alloc((uint64_t)search_grid * S * 4));
-    CK(order.alloc((uint64_t)search_grid * B * 4));
+    CK(order.alloc((uint64_t)search_grid * B * 8));
+    CK(ohash.alloc((uint64_t)search_grid * S * 8));
     CK(status.alloc(P * 4));
     CK(flags.alloc(64));
     size_t sort_tmp = 0;
@@ -548,7 +764,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     CK(cub_tmp.alloc(sort_tmp));
     uint32_t *d_flags = flags.as<uint32_t>();   // [0] dup, [1] overfull, [2] next part, [3] span, [4..5] evictions
 
-    const size_t smem = kMaxBucket * 8 + ((S + 31) / 32) * 4 + (kMaxBucket + 1) * 4 + kSetSize * 4 + kPendingCap * 4 + 16 * 4;
+    const size_t smem = search_smem_bytes(S);
     Header h;
     h.n = n; h.P = P; h.S = S; h.B = B; h.C = prm.C; h.gamma = prm.gamma; h.reduce = reduce;
     h.key_kind = key_kind; h.lambda = prm.lambda; h.alpha = prm.alpha; h.remap_len = total - n;
@@ -590,7 +806,8 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
         CK(cudaMemsetAsync(pilots.p, 0, nbkt, s));
         SearchArgs a;
         a.sorted = sorted.as<uint64_t>(); a.bstart = bstart.as<uint32_t>(); a.pilots = pilots.as<uint8_t>();
-        a.taken = taken.as<uint32_t>(); a.owner_scratch = owner.as<uint32_t>(); a.order_scratch = order.as<uint32_t>();
+        a.taken = taken.as<uint32_t>(); a.owner_scratch = owner.as<uint32_t>(); a.order_scratch = order.as<uint64_t>();
+        a.ohash_scratch = ohash.as<uint64_t>();
         a.status = status.as<uint32_t>();
         a.evictions = reinterpret_cast<unsigned long long *>(d_flags + 4);
         a.next_part = d_flags + 2;
@@ -761,7 +978,7 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
     int reduce;
     int rc = choose_layout(n, prm.lambda, prm.alpha, prm.slots_override, &P, &S, &B, &reduce);
     if (rc) return rc;
-    if (S > kMaxSlots || P > kNoAllocMaxParts) {
+    if (S > kMaxSlots || P > kNoAllocMaxParts || B > kOwnerMask) {
         set_error("layout P=%llu S=%llu exceeds this entry point's limits", (unsigned long long)P, (unsigned long long)S);
         return MPHF_ERR_CAPACITY;
     }
@@ -785,7 +1002,8 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
     uint8_t *pilots = c.take<uint8_t>(nbkt);
     uint32_t *taken = c.take<uint32_t>((words + 1) * 4);
     uint32_t *owner = c.take<uint32_t>((uint64_t)search_grid * S * 4);
-    uint32_t *order = c.take<uint32_t>((uint64_t)search_grid * B * 4);
+    uint64_t *order = c.take<uint64_t>((uint64_t)search_grid * B * 8);
+    uint64_t *ohash = c.take<uint64_t>((uint64_t)search_grid * S * 8);
     uint32_t *status = c.take<uint32_t>(P * 4);
     uint32_t *flags = c.take<uint32_t>(64);
     uint32_t *free_cnt = c.take<uint32_t>(words * 4), *high_cnt = c.take<uint32_t>(words * 4);
@@ -793,12 +1011,12 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
     uint32_t *L = c.take<uint32_t>(len * 4), *F = c.take<uint32_t>(len * 4);
     uint8_t *lines_buf = c.take<uint8_t>(lines * 64);
     if (!lines_buf || !F || !L || !high_rank || !free_rank || !high_cnt || !free_cnt || !flags || !status || !order ||
-        !owner || !taken || !pilots || !bstart || !scan_buf || !sort_buf || !sorted || !hash) {
+        !ohash || !owner || !taken || !pilots || !bstart || !scan_buf || !sort_buf || !sorted || !hash) {
         set_error("this layout needs more than the %llu-byte scratch array", (unsigned long long)kNoAllocScratchBytes);
         return MPHF_ERR_CAPACITY;
     }
 
-    const size_t smem = kMaxBucket * 8 + ((S + 31) / 32) * 4 + (kMaxBucket + 1) * 4 + kSetSize * 4 + kPendingCap * 4 + 16 * 4;
+    const size_t smem = search_smem_bytes(S);
     Header h;
     h.n = n; h.P = P; h.S = S; h.B = B; h.C = prm.C; h.gamma = prm.gamma; h.reduce = reduce;
     h.key_kind = MPHF_KEY_U64; h.lambda = prm.lambda; h.alpha = prm.alpha; h.remap_len = len;
@@ -830,7 +1048,7 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
         CK(cudaMemsetAsync(pilots, 0, nbkt, s));
         SearchArgs a;
         a.sorted = sorted; a.bstart = bstart; a.pilots = pilots; a.taken = taken; a.owner_scratch = owner;
-        a.order_scratch = order; a.status = status;
+        a.order_scratch = order; a.ohash_scratch = ohash; a.status = status;
         a.evictions = reinterpret_cast<unsigned long long *>(flags + 4);
         a.next_part = flags + 2;
         a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;

@@ -42,6 +42,16 @@ def test_gpu_build_is_bijective(n, params):
     assert np.array_equal(u32(N.mphf_query_u64(m2, keys)), u32(N.mphf_query_u64(m, keys)))
 
 
+@pytest.mark.parametrize("n", [50_000, 3 * 10**6])
+def test_gpu_build_is_deterministic(n):
+    """The same keys and parameters give the same structure, byte for byte."""
+    N = need_gpu()
+    keys = W.u64_keys(n, 8).cuda()
+    a = N.mphf_serialize(N.mphf_build(keys))
+    b = N.mphf_serialize(N.mphf_build(keys))
+    assert a == b
+
+
 def test_gpu_build_remap_invariants():
     """Keys mapping to slots >= n go, in slot order, to the free slots < n (Sec. 3.4)."""
     N = need_gpu()
