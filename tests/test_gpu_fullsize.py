@@ -1,0 +1,107 @@
+"""Parity at the full workload sizes, in the launch configurations bench.py
+times.  The oracle builds each structure on the host cores; the GPU
+evaluates every key; the whole output is checked to be a bijection (a
+property that holds at any size) and a seeded sample of outputs, plus the
+first and last positions, is compared with the oracle's one-by-one
+evaluation of the same keys.  Slow: about a minute each on 16 host cores."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2502_15539_gb300 import workloads as W
+from tests.gpu_common import need_gpu, u32
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+CORES = os.cpu_count() or 1
+
+
+def sample_positions(n: int, m: int = 1_000_000, seed: int = 5) -> torch.Tensor:
+    edges = torch.cat([torch.arange(min(n, 1000)), torch.arange(max(0, n - 1000), n)])
+    return torch.unique(torch.cat([W.uniform_index(m, n, seed), edges]))
+
+
+def assert_bijection_on_device(out: torch.Tensor, n: int):
+    seen = torch.zeros(n, dtype=torch.int32, device=out.device)
+    seen.index_fill_(0, out.to(torch.int64) & 0xFFFFFFFF, 1)
+    assert int(seen.sum().item()) == n
+    del seen
+
+
+def test_u64_1e9_keys():
+    """n = 1e9 distinct u64 keys, Default parameters, all keys queried in a
+    seeded random order with one mphf_query_u64 launch (the bench step)."""
+    N = need_gpu()
+    n = 10**9
+    keys = W.u64_keys(n, seed=0, device="cuda")
+    ref = O.OracleMPHF.build_u64(W.as_uint64_numpy(keys), threads=CORES)
+    m = N.mphf_deserialize(ref.serialize())
+    q = keys[W.permutation(n, seed=1, device="cuda")]
+    del keys
+    torch.cuda.empty_cache()
+    out = N.mphf_query_u64(m, q)
+    torch.cuda.synchronize()
+    assert_bijection_on_device(out, n)
+    idx = sample_positions(n).cuda()
+    got = u32(out[idx])
+    want = ref.query_u64(W.as_uint64_numpy(q[idx]), threads=CORES)
+    assert np.array_equal(got, want)
+
+
+def test_strings_3e8_keys():
+    """n = 3e8 printable strings of length U[16, 64], packed with u64 offsets;
+    all queried, re-packed in a seeded random order (the bench's string pass)."""
+    N = need_gpu()
+    n = 3 * 10**8
+    data, off = W.strings(torch.arange(n, device="cuda"), seed=0)
+    hd = data.cpu().numpy()
+    ho = off.cpu().numpy().view(np.uint64)
+    del data, off
+    torch.cuda.empty_cache()
+    ref = O.OracleMPHF.build_bytes(hd, ho, threads=CORES)
+    del hd, ho
+    m = N.mphf_deserialize(ref.serialize())
+    perm = W.permutation(n, seed=1, device="cuda")
+    qd, qo = W.strings(perm, seed=0)
+    out = N.mphf_query_bytes(m, qd, qo)
+    torch.cuda.synchronize()
+    del qd, qo
+    torch.cuda.empty_cache()
+    assert_bijection_on_device(out, n)
+    idx = sample_positions(n, m=300_000).cuda()
+    sd, so = W.strings(perm[idx].cpu(), seed=0)
+    got = u32(out[idx])
+    want = ref.query_bytes(sd.numpy(), so.numpy().astype(np.uint64), threads=CORES)
+    assert np.array_equal(got, want)
+
+
+def test_batch_256_structures():
+    """The batching workload: 256 structures with n log-uniform in [1e3, 1e7],
+    one request each of log-uniform size in [1, 1e6] (90% members), one
+    persistent launch; every output compared with the oracle."""
+    N = need_gpu()
+    k = 256
+    ns = W.log_uniform_int(k, 1e3, 1e7, seed=2).tolist()
+    qs = W.log_uniform_int(k, 1, 1e6, seed=3).tolist()
+    refs, items, queries = [], [], []
+    for i, (n, qn) in enumerate(zip(ns, qs)):
+        keys = W.u64_keys(n, seed=1000 + i)
+        ref = O.OracleMPHF.build_u64(W.as_uint64_numpy(keys), threads=CORES)
+        nm = qn // 10
+        q = torch.cat([keys[W.uniform_index(qn - nm, n, seed=2000 + i)], W.nonmember_u64_keys(nm, n, seed=1000 + i)])
+        m = N.mphf_deserialize(ref.serialize())
+        refs.append(ref)
+        queries.append(q)
+        items.append((m, q.cuda(), torch.full((qn,), -1, dtype=torch.int32, device="cuda")))
+    arr, keep = N.make_requests(items)
+    b = N.Batch(k)
+    b.autotune(arr, k)
+    b.run(arr, k)
+    torch.cuda.synchronize()
+    for ref, q, (_, _, out) in zip(refs, queries, items):
+        assert np.array_equal(u32(out), ref.query_u64(W.as_uint64_numpy(q), threads=CORES))
