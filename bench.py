@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--strings-n", type=float, default=3e8)
     ap.add_argument("--serve-requests", type=int, default=800)
     ap.add_argument("--batch-mphfs", type=int, default=256)
+    ap.add_argument("--batch-config", default="",
+                    help="keys_per_thread,threads,blocks_per_sm: fixed batch launch shape instead of autotuning")
     ap.add_argument("--query-keys", type=int, default=0,
                     help="query a seeded sample of this many member keys per step instead of all n "
                          "(small profiling case against the full-size structure)")
@@ -328,7 +330,12 @@ def run_batched(args, dev, stream):
     total = sum(qs)
     arr, keep = N.make_requests(items)
     b = N.Batch(k)
-    tuned = b.autotune(arr, k, os.path.join(tempfile.gettempdir(), "mphf_batch_tune.jsonl"), stream=stream)
+    if args.batch_config:
+        kpt, thr, bps = (int(x) for x in args.batch_config.split(","))
+        b.set_config(kpt, thr, bps, use_graph=True)
+        tuned = b.config()
+    else:
+        tuned = b.autotune(arr, k, os.path.join(tempfile.gettempdir(), "mphf_batch_tune.jsonl"), stream=stream)
 
     def timed(fn):
         for _ in range(args.warmup):

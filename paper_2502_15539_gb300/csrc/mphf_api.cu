@@ -99,10 +99,8 @@ int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_overri
     return MPHF_OK;
 }
 
-void fastmod_constant(uint64_t S, uint64_t *hi, uint64_t *lo) {
-    unsigned __int128 c = ~(unsigned __int128)0 / S + 1;   // ceil(2^128 / S), S not 2^k
-    *hi = (uint64_t)(c >> 64);
-    *lo = (uint64_t)c;
+uint64_t barrett_constant(uint64_t S) {
+    return (uint64_t)(((unsigned __int128)1 << 64) / S);   // floor(2^64 / S), S >= 2
 }
 
 uint64_t clef_lines_for(uint64_t remap_len) { return (remap_len + kClefPerLine - 1) / kClefPerLine; }
@@ -113,8 +111,8 @@ View make_view(const Header &h, const uint8_t *pilots, const void *remap) {
     v.remap = remap;
     v.n = h.n; v.P = h.P; v.S = h.S; v.B = h.B; v.C = h.C; v.seed = h.seed;
     v.s_mask = h.S - 1;
-    v.fm_hi = v.fm_lo = 0;
-    if (h.reduce == kReduceMod) fastmod_constant(h.S, &v.fm_hi, &v.fm_lo);
+    v.fm = v.fm_unused = 0;
+    if (h.reduce == kReduceMod) v.fm = barrett_constant(h.S);
     return v;
 }
 

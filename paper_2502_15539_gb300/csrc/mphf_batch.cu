@@ -54,7 +54,7 @@ __device__ __forceinline__ uint64_t bucket_any(const View &v, uint64_t h, uint64
 __device__ __forceinline__ uint32_t slot_any(const View &v, uint64_t h, uint64_t part, uint32_t pilot, bool pow2,
                                              int remap) {
     const uint64_t x = h ^ (v.C * ((uint64_t)pilot ^ v.seed));
-    const uint64_t r = pow2 ? (mul_hi(v.C, x) & v.s_mask) : mod_direct(x, v.fm_hi, v.fm_lo, v.S);
+    const uint64_t r = pow2 ? (mul_hi(v.C, x) & v.s_mask) : mod_barrett(x, v.fm, v.S);
     const uint64_t s = part * v.S + r;
     if (s < v.n) return (uint32_t)s;
     const uint32_t j = (uint32_t)(s - v.n);

@@ -79,13 +79,13 @@ struct SearchArgs {
     uint32_t *status;         // per part
     unsigned long long *evictions;
     uint32_t *next_part;
-    uint64_t P, S, B, C, seed, fm_hi, fm_lo, s_mask, evict_cap;
+    uint64_t P, S, B, C, seed, fm, s_mask, evict_cap;
 };
 
 template <int REDUCE>
 __device__ __forceinline__ uint32_t slot_in_part(const SearchArgs &a, uint64_t x) {
     if constexpr (REDUCE == kReducePow2) return (uint32_t)(mul_hi(a.C, x) & a.s_mask);
-    else return (uint32_t)mod_direct(x, a.fm_hi, a.fm_lo, a.S);
+    else return (uint32_t)mod_barrett(x, a.fm, a.S);
 }
 
 __device__ __forceinline__ bool bit_of(const uint32_t *bits, uint32_t s) { return (bits[s >> 5] >> (s & 31)) & 1u; }
@@ -812,8 +812,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
         a.evictions = reinterpret_cast<unsigned long long *>(d_flags + 4);
         a.next_part = d_flags + 2;
         a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;
-        a.fm_hi = a.fm_lo = 0;
-        if (reduce == kReduceMod) fastmod_constant(S, &a.fm_hi, &a.fm_lo);
+        a.fm = reduce == kReduceMod ? barrett_constant(S) : 0;
         a.evict_cap = (uint64_t)prm.evict_mult * S;
         CK(reduce == kReducePow2 ? launch_search<kReducePow2>(a, search_grid, smem, s)
                                  : launch_search<kReduceMod>(a, search_grid, smem, s));
@@ -1052,8 +1051,7 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
         a.evictions = reinterpret_cast<unsigned long long *>(flags + 4);
         a.next_part = flags + 2;
         a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;
-        a.fm_hi = a.fm_lo = 0;
-        if (reduce == kReduceMod) fastmod_constant(S, &a.fm_hi, &a.fm_lo);
+        a.fm = reduce == kReduceMod ? barrett_constant(S) : 0;
         a.evict_cap = (uint64_t)prm.evict_mult * S;
         CK(reduce == kReducePow2 ? launch_search<kReducePow2>(a, search_grid, smem, s)
                                  : launch_search<kReduceMod>(a, search_grid, smem, s));

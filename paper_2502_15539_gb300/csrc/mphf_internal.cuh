@@ -24,7 +24,7 @@ struct View {
     const uint8_t *pilots;   // P*B bytes
     const void *remap;       // CacheLineEF lines (64 B each) or u32 entries
     uint64_t n, P, S, B, C, seed;
-    uint64_t fm_hi, fm_lo;   // ceil(2^128 / S) for reduce = x mod S
+    uint64_t fm, fm_unused;  // floor(2^64 / S) for reduce = x mod S
     uint64_t s_mask;         // S - 1 for power-of-two S
 };
 
@@ -45,7 +45,7 @@ void count_launch(uint64_t k = 1);
 // Layout rule of Sec. 3.1 "Parameter values" (library's own implementation).
 int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_override,
                   uint64_t *P, uint64_t *S, uint64_t *B, int *reduce);
-void fastmod_constant(uint64_t S, uint64_t *hi, uint64_t *lo);
+uint64_t barrett_constant(uint64_t S);
 uint64_t clef_lines_for(uint64_t remap_len);
 
 View make_view(const Header &h, const uint8_t *pilots, const void *remap);
@@ -88,16 +88,14 @@ __device__ __forceinline__ uint64_t bucket_fn(uint64_t x) {
     }
 }
 
-// x mod S for S < 2^32 by direct computation of the remainder (Lemire,
-// Kaser, Kurz 2019): with c = ceil(2^128 / S), x mod S = ((c x mod 2^128) S) >> 128.
-__device__ __forceinline__ uint64_t mod_direct(uint64_t x, uint64_t c_hi, uint64_t c_lo,
-                                               uint64_t S) {
-    uint64_t l0 = c_lo * x;
-    uint64_t l1 = mul_hi(c_lo, x) + c_hi * x;   // (c x) mod 2^128 = (l1, l0)
-    uint64_t b1 = mul_hi(l0, S);
-    uint64_t d0 = l1 * S;
-    uint64_t d1 = mul_hi(l1, S);
-    return d1 + ((d0 + b1) < d0 ? 1u : 0u);
+// x mod S for 2 <= S < 2^32 by Barrett reduction: with M = floor(2^64 / S),
+// q = hi(x M) is floor(x / S) or one less (x M / 2^64 > x / S - 1), so
+// x - q S lies in [0, 2S) and one conditional subtraction makes it exact.
+__device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t M, uint64_t S) {
+    const uint64_t q = mul_hi(x, M);
+    uint64_t r = x - q * S;
+    if (r >= S) r -= S;
+    return r;
 }
 
 template <int REDUCE>
@@ -105,7 +103,7 @@ __device__ __forceinline__ uint64_t reduce_slot(const View &v, uint64_t x) {
     if constexpr (REDUCE == kReducePow2) {
         return mul_hi(v.C, x) & v.s_mask;      // hi(C x) mod S, S = 2^k
     } else {
-        return mod_direct(x, v.fm_hi, v.fm_lo, v.S);
+        return mod_barrett(x, v.fm, v.S);
     }
 }
 

@@ -136,15 +136,15 @@ __device__ __forceinline__ uint64_t str_finish(uint64_t acc, uint64_t len, uint6
     return str_mix(acc ^ (len * kStrK2) ^ seed);
 }
 
-// Word j of a string that starts `start` bytes into an 8-byte-aligned buffer.
-__device__ __forceinline__ uint64_t load_word(const uint64_t *buf, uint64_t start, uint64_t j,
-                                              uint64_t len) {
-    const uint64_t pos = start + 8 * j;
-    const uint64_t a = pos >> 3;
-    const uint32_t sh = (uint32_t)(pos & 7) * 8;
+// Word j of a string that starts `start` bytes into an 8-byte-aligned buffer
+// (positions inside the shared-memory stage fit 32 bits).
+__device__ __forceinline__ uint64_t load_word(const uint64_t *buf, uint32_t start, uint32_t j, uint32_t len) {
+    const uint32_t pos = start + 8 * j;
+    const uint32_t a = pos >> 3;
+    const uint32_t sh = (pos & 7) * 8;
     uint64_t w = buf[a] >> sh;
     if (sh) w |= buf[a + 1] << (64 - sh);
-    const uint64_t rem = len - 8 * j;
+    const uint32_t rem = len - 8 * j;
     if (rem < 8) w &= (1ull << (8 * rem)) - 1;
     return w;
 }
@@ -184,13 +184,16 @@ query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64
     const bool staged = hi - base + 32 <= kStrStage;   // + one zeroed chunk
     uint64_t h;
     if (staged) {
-        const uint64_t nvec = (hi - base + 15) / 16;
+        // Every byte below the end of the whole key buffer may be read; only a
+        // chunk that crosses it is read byte by byte.
+        const uint64_t end_all = last < count ? __ldg(offsets + count) : hi;
+        const uint32_t nvec = (uint32_t)((hi - base + 15) / 16);
         uint4 *dst = reinterpret_cast<uint4 *>(stage[warp]);
-        for (uint64_t q = lane; q < nvec; q += 32) {
-            const uint64_t c0 = base + 16 * q;
-            if (c0 + 16 <= hi) {
+        for (uint32_t q = lane; q < nvec; q += 32) {
+            const uint64_t c0 = base + 16ull * q;
+            if (c0 + 16 <= end_all) {
                 dst[q] = __ldcs(reinterpret_cast<const uint4 *>(bytes + c0));
-            } else {   // the last chunk: read no byte past the end of the keys
+            } else {
                 uint8_t *d8 = stage[warp] + 16 * q;
                 for (int t = 0; t < 16; t++) d8[t] = c0 + t < hi ? __ldg(bytes + c0 + t) : 0;
             }
@@ -198,9 +201,9 @@ query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64
         if (lane == 0) dst[nvec] = make_uint4(0, 0, 0, 0);   // word a+1 may be read
         __syncwarp();
         const uint64_t *buf = reinterpret_cast<const uint64_t *>(stage[warp]);
-        const uint64_t len = e - a, start = a - base;
-        uint64_t acc = 0;
-        for (uint64_t j = 0; 8 * j < len; j++) acc += str_mix(load_word(buf, start, j, len) ^ (v.seed + j * kStrK1));
+        const uint32_t len = (uint32_t)(e - a), start = (uint32_t)(a - base);
+        uint64_t acc = 0, tweak = v.seed;   // tweak = seed + j K1
+        for (uint32_t j = 0; 8 * j < len; j++, tweak += kStrK1) acc += str_mix(load_word(buf, start, j, len) ^ tweak);
         h = str_finish(acc, len, v.seed);
     } else {
         h = hash_string_global(bytes, a, e - a, v.seed);
