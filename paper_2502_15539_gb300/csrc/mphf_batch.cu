@@ -62,26 +62,6 @@ __device__ __forceinline__ uint32_t slot_any(const View &v, uint64_t h, uint64_t
     return __ldg(static_cast<const uint32_t *>(v.remap) + j);
 }
 
-__device__ __forceinline__ uint64_t batch_str_mix(uint64_t z) {
-    z ^= z >> 30;
-    z *= 0xBF58476D1CE4E5B9ull;
-    z ^= z >> 27;
-    z *= 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return z;
-}
-
-// The project string hash (same definition as the single-structure query).
-__device__ uint64_t batch_string_hash(const uint8_t *bytes, uint64_t a, uint64_t len, uint64_t seed) {
-    uint64_t acc = 0;
-    for (uint64_t j = 0; 8 * j < len; j++) {
-        uint64_t w = 0;
-        for (uint32_t t = 0; t < 8 && 8 * j + t < len; t++) w |= (uint64_t)__ldg(bytes + a + 8 * j + t) << (8 * t);
-        acc += batch_str_mix(w ^ (seed + j * 0x9E3779B97F4A7C15ull));
-    }
-    return batch_str_mix(acc ^ (len * 0xC2B2AE3D27D4EB4Full) ^ seed);
-}
-
 constexpr int kMaxReqSmem = 4096;   // request tile starts cached in shared memory
 
 // Persistent CTAs; tile t of request r covers keys [(t - first_tile[r]) * TK, ...).
@@ -91,6 +71,7 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
                    BatchHeader *__restrict__ hdr) {
     __shared__ uint32_t s_first[kMaxReqSmem + 1];
     __shared__ uint32_t s_tile;
+    extern __shared__ __align__(16) uint8_t s_stage[];   // kStrStage bytes per warp
     const uint32_t nreq = hdr->nreq, total = hdr->total_tiles;
     for (uint32_t i = threadIdx.x; i <= nreq && i <= kMaxReqSmem; i += blockDim.x) s_first[i] = first_tile[i];
     __syncthreads();
@@ -133,16 +114,21 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
                 if (i < d.count) __stcs(d.out + i, slot_any(v, h[q], part[q], p[q], pow2, remap));
             }
         } else {
+            // Strings: each warp hashes groups of 32 consecutive strings of the
+            // tile through its shared-memory stage.
             const uint8_t *bytes = static_cast<const uint8_t *>(d.keys);
-#pragma unroll 1
-            for (int q = 0; q < K; q++) {
-                const uint64_t i = base + (uint64_t)q * blockDim.x + threadIdx.x;
-                if (i >= d.count) break;
-                const uint64_t a = __ldg(d.offsets + i), e = __ldg(d.offsets + i + 1);
-                const uint64_t hh = batch_string_hash(bytes, a, e - a, v.seed);
-                uint64_t pt;
-                const uint64_t bb = bucket_any(v, hh, pt, cubic);
-                d.out[i] = slot_any(v, hh, pt, __ldg(v.pilots + bb), pow2, remap);
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+            uint8_t *stage = s_stage + (size_t)warp * kStrStage;
+            for (int g = warp; g < K * nwarps; g += nwarps) {
+                const uint64_t w0 = base + 32ull * g;
+                if (w0 >= d.count) break;
+                const uint64_t hh = warp_hash_strings(bytes, d.offsets, w0, d.count, stage, v.seed, lane);
+                const uint64_t i = w0 + lane;
+                if (i < d.count) {
+                    uint64_t pt;
+                    const uint64_t bb = bucket_any(v, hh, pt, cubic);
+                    d.out[i] = slot_any(v, hh, pt, __ldg(v.pilots + bb), pow2, remap);
+                }
             }
         }
     }
@@ -158,14 +144,30 @@ static bool valid_config(const BatchConfig &c) {
            (c.threads == 128 || c.threads == 256 || c.threads == 512) && c.blocks_per_sm >= 1 && c.blocks_per_sm <= 16;
 }
 
+template <int K>
+static void launch_k(unsigned grid, int threads, size_t smem, const BatchDesc *desc, const uint32_t *first,
+                     BatchHeader *hdr, cudaStream_t s) {
+    // Static + dynamic shared memory can exceed 48 KB: opt in once per device.
+    static std::atomic<uint64_t> opted{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(opted.load(std::memory_order_relaxed) & bit)) {
+        cudaFuncSetAttribute(batch_query_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kStrStage);
+        opted.fetch_or(bit, std::memory_order_relaxed);
+    }
+    batch_query_kernel<K><<<grid, threads, smem, s>>>(desc, first, hdr);
+}
+
 static cudaError_t launch_batch_kernel(const BatchConfig &c, int sms, const BatchDesc *desc, const uint32_t *first,
                                        BatchHeader *hdr, cudaStream_t s) {
     const unsigned grid = (unsigned)(sms * c.blocks_per_sm);
+    const size_t smem = (size_t)(c.threads / 32) * kStrStage;
     switch (c.keys_per_thread) {
-        case 2: batch_query_kernel<2><<<grid, c.threads, 0, s>>>(desc, first, hdr); break;
-        case 4: batch_query_kernel<4><<<grid, c.threads, 0, s>>>(desc, first, hdr); break;
-        case 16: batch_query_kernel<16><<<grid, c.threads, 0, s>>>(desc, first, hdr); break;
-        default: batch_query_kernel<8><<<grid, c.threads, 0, s>>>(desc, first, hdr); break;
+        case 2: launch_k<2>(grid, c.threads, smem, desc, first, hdr, s); break;
+        case 4: launch_k<4>(grid, c.threads, smem, desc, first, hdr, s); break;
+        case 16: launch_k<16>(grid, c.threads, smem, desc, first, hdr, s); break;
+        default: launch_k<8>(grid, c.threads, smem, desc, first, hdr, s); break;
     }
     count_launch();
     return cudaGetLastError();

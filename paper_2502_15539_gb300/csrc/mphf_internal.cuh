@@ -139,4 +139,88 @@ __device__ __forceinline__ uint32_t clef_get(const uint8_t *lines, uint32_t j) {
     return 256u * (offset + sel - i) + low;
 }
 
+// ------------------------------------------------------------ string keys
+// Project string hash (the paper's GxHash is not specified in it):
+//   w_j = little-endian u64 of bytes [8j, 8j+8) zero-padded past len,
+//   acc = sum_j mix(w_j xor (seed + j K1)),  h = mix(acc xor len K2 xor seed),
+// mix = splitmix64 finalizer.  The sum lets every word be hashed on its own.
+__device__ __forceinline__ uint64_t str_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+constexpr uint64_t kStrK1 = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kStrK2 = 0xC2B2AE3D27D4EB4Full;
+
+__device__ __forceinline__ uint64_t str_finish(uint64_t acc, uint64_t len, uint64_t seed) {
+    return str_mix(acc ^ (len * kStrK2) ^ seed);
+}
+
+// Word j of a string that starts `start` bytes into an 8-byte-aligned buffer
+// (positions inside the shared-memory stage fit 32 bits).
+__device__ __forceinline__ uint64_t load_word(const uint64_t *buf, uint32_t start, uint32_t j, uint32_t len) {
+    const uint32_t pos = start + 8 * j;
+    const uint32_t a = pos >> 3;
+    const uint32_t sh = (pos & 7) * 8;
+    uint64_t w = buf[a] >> sh;
+    if (sh) w |= buf[a + 1] << (64 - sh);
+    const uint32_t rem = len - 8 * j;
+    if (rem < 8) w &= (1ull << (8 * rem)) - 1;
+    return w;
+}
+
+__device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uint64_t a, uint64_t len,
+                                                       uint64_t seed) {
+    uint64_t acc = 0;
+    for (uint64_t j = 0; 8 * j < len; j++) {
+        uint64_t w = 0;
+        for (uint32_t t = 0; t < 8 && 8 * j + t < len; t++) w |= (uint64_t)__ldg(bytes + a + 8 * j + t) << (8 * t);
+        acc += str_mix(w ^ (seed + j * kStrK1));
+    }
+    return str_finish(acc, len, seed);
+}
+
+constexpr int kStrStage = 2048 + 32;   // staged bytes per warp (32 strings)
+
+// Hashes the strings [w0, min(w0 + 32, count)) of a warp: lane l returns the
+// hash of string w0 + l (any value for lanes past count).  Their contiguous
+// byte range is staged into `stage` (kStrStage bytes, 16-byte aligned,
+// private to the warp) with 16-byte loads; every byte below the end of the
+// whole key buffer may be read, only a chunk crossing it is read byte by
+// byte.  A warp whose range does not fit the stage reads from global memory.
+// All lanes of the warp must call it.
+__device__ __forceinline__ uint64_t warp_hash_strings(const uint8_t *bytes, const uint64_t *offsets, uint64_t w0,
+                                                      uint64_t count, uint8_t *stage, uint64_t seed, int lane) {
+    const uint64_t i = w0 + lane;
+    const uint64_t last = (w0 + 32 < count ? w0 + 32 : count);
+    const uint64_t lo = __ldg(offsets + w0), hi = __ldg(offsets + last);
+    const uint64_t a = i < count ? __ldg(offsets + i) : hi;
+    const uint64_t e = i < count ? __ldg(offsets + i + 1) : hi;
+    const uint64_t base = lo & ~15ull;
+    if (hi - base + 32 > kStrStage) return hash_string_global(bytes, a, e - a, seed);   // + one zeroed chunk
+    const uint64_t end_all = last < count ? __ldg(offsets + count) : hi;
+    const uint32_t nvec = (uint32_t)((hi - base + 15) / 16);
+    uint4 *dst = reinterpret_cast<uint4 *>(stage);
+    __syncwarp();   // the stage may still be read from a previous call
+    for (uint32_t q = lane; q < nvec; q += 32) {
+        const uint64_t c0 = base + 16ull * q;
+        if (c0 + 16 <= end_all) {
+            dst[q] = __ldcs(reinterpret_cast<const uint4 *>(bytes + c0));
+        } else {
+            uint8_t *d8 = stage + 16 * q;
+            for (int t = 0; t < 16; t++) d8[t] = c0 + t < hi ? __ldg(bytes + c0 + t) : 0;
+        }
+    }
+    if (lane == 0) dst[nvec] = make_uint4(0, 0, 0, 0);   // word a+1 may be read
+    __syncwarp();
+    const uint64_t *buf = reinterpret_cast<const uint64_t *>(stage);
+    const uint32_t len = (uint32_t)(e - a), start = (uint32_t)(a - base);
+    uint64_t acc = 0, tweak = seed;   // tweak = seed + j K1
+    for (uint32_t j = 0; 8 * j < len; j++, tweak += kStrK1) acc += str_mix(load_word(buf, start, j, len) ^ tweak);
+    return str_finish(acc, len, seed);
+}
+
 }  // namespace ptrhash
