@@ -128,6 +128,18 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def aggregate_ranks(local_ms: float, keys_per_rank: int, steps: int, ws: int, device) -> tuple[float, float]:
+    """Whole-job throughput over replicas: every rank's keys over the slowest
+    rank's time (max over ranks of the timed region)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total = float(t.item())
+    return total, ws * keys_per_rank * steps / (total / 1e3)
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -207,13 +219,8 @@ def run_gpu(args):
         barrier()
     launches = N.mphf_launch_count() - launches0
     clocks = clk.summary()
-    total_ms = sum(per_step)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms, value = aggregate_ranks(sum(per_step), mq, args.steps, ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * mq * args.steps / (total_ms / 1e3)
 
     # Random-gather probe: same key stream, table the size of the pilot array.
     table = torch.randint(0, 256, (info["pilot_bytes"],), dtype=torch.uint8, device=dev)

@@ -23,6 +23,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ptrhash_oracle.c")
 _LIB = os.path.join(_HERE, "libptrhash_oracle.so")
+# A prebuilt library to load instead (the mutation tests load planted mistakes this way).
+_LIB_OVERRIDE = os.environ.get("PTRHASH_ORACLE_LIB")
 
 OK = 0
 ERR_ARG = -1
@@ -70,6 +72,8 @@ _lib = None
 
 def build_library(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (plain C11 + pthreads)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "ptrhash_oracle.h"))):
         tmp = _LIB + f".tmp{os.getpid()}"

@@ -1,0 +1,54 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake (a dropped term, a wrong operand, a wrong
+index) in a copy of the oracle's C source, builds it, and runs the pin
+tests against it in a subprocess: at least one pin must fail.  The real
+oracle is untouched."""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ptrhash_oracle.c")
+
+MUTATIONS = {
+    "part uses lo instead of hi": ("*part = orc_hi(L->P, h);", "*part = orc_lo(L->P, h);"),
+    "gamma3 drops the x/256 term": ("return half_sum - (half_sum >> 8) + (x >> 8);",
+                                    "return half_sum - (half_sum >> 8);"),
+    "gamma3 cube from the wrong operand": ("uint64_t x3 = orc_hi(x2, x);", "uint64_t x3 = orc_hi(x2, x2);"),
+    "slot drops the part offset": ("return part * m->L.S + orc_reduce(m->L.reduce, m->C, x, m->L.S);",
+                                   "return orc_reduce(m->L.reduce, m->C, x, m->L.S);"),
+    "reduce uses lo instead of hi": ("if (reduce == ORC_REDUCE_POW2) return orc_hi(C, x) % S;",
+                                     "if (reduce == ORC_REDUCE_POW2) return orc_lo(C, x) % S;"),
+    "pilot hash adds instead of xor": ("return C * (pilot ^ seed); }", "return C * (pilot + seed); }"),
+    "clef lookup drops -i": ("return 256 * (offset + sel - i) + line[20 + i];",
+                             "return 256 * (offset + sel) + line[20 + i];"),
+    "clef encode drops the index bit": ("uint64_t bit = i + ((v[i] >> 8) - offset);",
+                                        "uint64_t bit = (v[i] >> 8) - offset;"),
+    "remap without predecessor fill": ("        else F[j] = prev;\n", "\n"),
+    "buckets per part ignore alpha": ("uint64_t B = (uint64_t)ceil(alpha * (double)S / lambda);",
+                                      "uint64_t B = (uint64_t)ceil((double)S / lambda);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found: {name}"
+    mutant = tmp_path / "ptrhash_oracle.c"
+    mutant.write_text(src.replace(old, new))
+    (tmp_path / "ptrhash_oracle.h").write_text(open(os.path.join(ROOT, "oracle", "ptrhash_oracle.h")).read())
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-fPIC", "-shared", "-pthread", "-o", str(lib),
+                           str(mutant), "-lm"])
+    env = dict(os.environ, PTRHASH_ORACLE_LIB=str(lib))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, f"no pin caught: {name}\n{res.stdout[-2000:]}"
