@@ -329,6 +329,29 @@ void mphf_server_free(mphf_server_t *s);
 int mphf_build_u64_noalloc(const mphf_params *params, const uint64_t *keys_dev, uint64_t n,
                            void *out_host, size_t cap, size_t *needed, void *stream);
 
+/* -------------------------------------------------- device-side view */
+/* Everything a kernel needs to evaluate a structure (see mphf_device.cuh):
+ * device pointers into the structure's memory plus its layout. */
+typedef struct {
+    const uint8_t *pilots;     /* P*B pilot bytes (device)                       */
+    const void    *remap;      /* CacheLineEF lines or u32 entries (device)      */
+    uint64_t n, P, S, B, C, seed;
+    uint64_t barrett;          /* floor(2^64 / S) when reduce = x mod S          */
+    uint64_t s_mask;           /* S - 1 when S is a power of two                 */
+    int32_t  gamma;            /* MPHF_GAMMA_*                                   */
+    int32_t  reduce;           /* 0: S = 2^k, reduce(x) = hi(C x) & (S - 1);
+                                  1: reduce(x) = x mod S (Sec. 3.1)              */
+    int32_t  remap_kind;       /* MPHF_REMAP_*                                   */
+    int32_t  key_kind;         /* MPHF_KEY_*                                     */
+} mphf_view_t;
+
+/* Fills *out with the structure's device view, for fusing the evaluation
+ * into a caller's own kernels through include/mphf_device.cuh (no paper
+ * counterpart; the paper's conclusion asks for streaming queries inside
+ * applications).  The view stays valid until mphf_free(m).  Errors:
+ * MPHF_ERR_ARG. */
+int mphf_device_view(const mphf_t *m, mphf_view_t *out);
+
 /* Number of kernel launches this library issued since it was loaded
  * (all entry points, all threads). */
 uint64_t mphf_launch_count(void);

@@ -1,0 +1,141 @@
+/*
+ * mphf_device.cuh -- evaluate a PtrHash structure inside your own kernels.
+ *
+ * Header-only CUDA device code.  Get a structure's view on the host with
+ * mphf_device_view() (include/mphf.h), pass it to your kernel by value, and
+ * call mphf_dev::eval_u64 / eval_bytes / eval_hash per key: the result is the
+ * same as mphf_query_u64 / mphf_query_bytes on that key, so an application
+ * can fuse the lookup into the kernel that produces or consumes its keys
+ * (streaming queries inside an application, the direction the paper's
+ * conclusion proposes).  The view's device memory belongs to the structure:
+ * keep the structure alive while kernels use the view.  The same arithmetic
+ * is what libmphf's own kernels run (Sec. 3.1 Eq. partbucket / Eq. slot,
+ * Sec. 3.3 gamma, Sec. 3.4 CacheLineEF).
+ */
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mphf.h"
+
+namespace mphf_dev {
+
+__device__ __forceinline__ uint64_t mul_hi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+// gamma on 64-bit fixed point (Sec. 3.3): gamma_1(x) = x, gamma_3(x) =
+// 255/256 (x^2 + x^3)/2 + x/256 with x^2 = hi(x x), x^3 = hi(x^2 x), floors.
+template <int GAMMA>
+__device__ __forceinline__ uint64_t bucket_fn(uint64_t x) {
+    if constexpr (GAMMA == MPHF_GAMMA_LINEAR) {
+        return x;
+    } else {
+        uint64_t sq = mul_hi(x, x);
+        uint64_t cube = mul_hi(sq, x);
+        uint64_t half = (sq >> 1) + (cube >> 1);
+        return half - (half >> 8) + (x >> 8);
+    }
+}
+
+// x mod S for 2 <= S < 2^32 by Barrett reduction: with M = floor(2^64 / S),
+// q = hi(x M) is floor(x / S) or one less (x M / 2^64 > x / S - 1), so
+// x - q S lies in [0, 2S) and one conditional subtraction makes it exact.
+__device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t M, uint64_t S) {
+    const uint64_t q = mul_hi(x, M);
+    uint64_t r = x - q * S;
+    if (r >= S) r -= S;
+    return r;
+}
+
+// Position of the i-th (0-based) set bit of a 32-bit word that has > i set bits.
+__device__ __forceinline__ uint32_t select32(uint32_t w, uint32_t i) {
+    uint32_t pos = 0, c;
+    c = __popc(w & 0xFFFFu); if (i >= c) { i -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xFFu);   if (i >= c) { i -= c; w >>= 8;  pos += 8; }
+    c = __popc(w & 0xFu);    if (i >= c) { i -= c; w >>= 4;  pos += 4; }
+    c = __popc(w & 0x3u);    if (i >= c) { i -= c; w >>= 2;  pos += 2; }
+    c = w & 1u;              if (i >= c) { pos += 1; }
+    return pos;
+}
+
+// CacheLineEF lookup (Sec. 3.4): v = 256 (offset + select(i) - i) + low[i].
+// Line layout: bytes 0..15 the 128-bit bitmap (two little-endian words),
+// 16..19 the offset, 20..63 the low bytes.
+__device__ __forceinline__ uint32_t clef_get(const uint8_t *lines, uint32_t j) {
+    uint32_t line = j / 44u;
+    uint32_t i = j - line * 44u;
+    const uint8_t *L = lines + (uint64_t)line * 64;
+    uint4 head = __ldg(reinterpret_cast<const uint4 *>(L));        // bitmap words
+    uint32_t offset = __ldg(reinterpret_cast<const uint32_t *>(L + 16));
+    uint32_t low = __ldg(L + 20 + i);
+    uint32_t words[4] = {head.x, head.y, head.z, head.w};
+    uint32_t sel = 0, k = i;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        uint32_t c = __popc(words[q]);
+        if (k < c) { sel = 32 * q + select32(words[q], k); break; }
+        k -= c;
+    }
+    return 256u * (offset + sel - i) + low;
+}
+
+// ------------------------------------------------------------ string keys
+// Project string hash (the paper's GxHash is not specified in it):
+//   w_j = little-endian u64 of bytes [8j, 8j+8) zero-padded past len,
+//   acc = sum_j mix(w_j xor (seed + j K1)),  h = mix(acc xor len K2 xor seed),
+// mix = splitmix64 finalizer.  The sum lets every word be hashed on its own.
+__device__ __forceinline__ uint64_t str_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+constexpr uint64_t kStrK1 = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kStrK2 = 0xC2B2AE3D27D4EB4Full;
+
+__device__ __forceinline__ uint64_t str_finish(uint64_t acc, uint64_t len, uint64_t seed) {
+    return str_mix(acc ^ (len * kStrK2) ^ seed);
+}
+
+__device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uint64_t a, uint64_t len,
+                                                       uint64_t seed) {
+    uint64_t acc = 0;
+    for (uint64_t j = 0; 8 * j < len; j++) {
+        uint64_t w = 0;
+        for (uint32_t t = 0; t < 8 && 8 * j + t < len; t++) w |= (uint64_t)__ldg(bytes + a + 8 * j + t) << (8 * t);
+        acc += str_mix(w ^ (seed + j * kStrK1));
+    }
+    return str_finish(acc, len, seed);
+}
+
+// The non-minimal slot of a key hash (Eq. slot): part S + reduce(h xor hp(p), S).
+__device__ __forceinline__ uint64_t slot_hash(const mphf_view_t &v, uint64_t h) {
+    const uint64_t part = mul_hi(v.P, h);
+    const uint64_t x = v.P * h;   // position inside the part, as a fraction of 2^64
+    const uint64_t g = v.gamma == MPHF_GAMMA_CUBIC ? bucket_fn<MPHF_GAMMA_CUBIC>(x) : x;
+    const uint64_t b = part * v.B + mul_hi(v.B, g);
+    const uint64_t xp = h ^ (v.C * ((uint64_t)__ldg(v.pilots + b) ^ v.seed));
+    const uint64_t r = v.reduce == 0 ? (mul_hi(v.C, xp) & v.s_mask) : mod_barrett(xp, v.barrett, v.S);
+    return part * v.S + r;
+}
+
+// The MPHF value of a key hash: the slot, or its remap entry when >= n.
+__device__ __forceinline__ uint32_t eval_hash(const mphf_view_t &v, uint64_t h) {
+    const uint64_t s = slot_hash(v, h);
+    if (s < v.n) return (uint32_t)s;
+    const uint32_t j = (uint32_t)(s - v.n);
+    if (v.remap_kind == MPHF_REMAP_CLEF) return clef_get(static_cast<const uint8_t *>(v.remap), j);
+    return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+}
+
+// A u64 key (structures built with MPHF_KEY_U64).
+__device__ __forceinline__ uint32_t eval_u64(const mphf_view_t &v, uint64_t key) { return eval_hash(v, v.C * key); }
+
+// A byte-string key (structures built with MPHF_KEY_BYTES).
+__device__ __forceinline__ uint32_t eval_bytes(const mphf_view_t &v, const uint8_t *s, uint64_t len) {
+    return eval_hash(v, hash_string_global(s, 0, len, v.seed));
+}
+
+}  // namespace mphf_dev

@@ -33,7 +33,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     include = os.path.join(os.path.dirname(HERE), "include")
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(include, "mphf.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(include, "mphf.h"),
+                                                         os.path.join(include, "mphf_device.cuh")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

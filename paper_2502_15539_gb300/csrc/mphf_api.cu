@@ -382,6 +382,19 @@ int mphf_info(const mphf_t *m, mphf_info_t *out) {
 
 void mphf_free(mphf_t *m) { free_handle(m); }
 
+int mphf_device_view(const mphf_t *m, mphf_view_t *out) {
+    if (!m || !out) { set_error("NULL argument"); return MPHF_ERR_ARG; }
+    const Header &h = m->hdr;
+    memset(out, 0, sizeof(*out));
+    out->pilots = m->d_pilots;
+    out->remap = m->d_remap;
+    out->n = h.n; out->P = h.P; out->S = h.S; out->B = h.B; out->C = h.C; out->seed = h.seed;
+    out->barrett = h.reduce == kReduceMod ? barrett_constant(h.S) : 0;
+    out->s_mask = h.S - 1;
+    out->gamma = h.gamma; out->reduce = h.reduce; out->remap_kind = h.remap; out->key_kind = h.key_kind;
+    return MPHF_OK;
+}
+
 int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
                    void *stream) {
     if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }

@@ -12,6 +12,7 @@
 #include <string>
 
 #include "../../include/mphf.h"
+#include "../../include/mphf_device.cuh"
 
 namespace ptrhash {
 
@@ -72,31 +73,9 @@ int build_structure(const mphf_params &p, int key_kind, const void *keys, const 
                     uint64_t n, cudaStream_t s, BuildResult *out);
 
 // ------------------------------------------------------------- device side
-__device__ __forceinline__ uint64_t mul_hi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
-
-// gamma on 64-bit fixed point (Sec. 3.3): gamma_1(x) = x, gamma_3(x) =
-// 255/256 (x^2 + x^3)/2 + x/256 with x^2 = hi(x x), x^3 = hi(x^2 x), floors.
-template <int GAMMA>
-__device__ __forceinline__ uint64_t bucket_fn(uint64_t x) {
-    if constexpr (GAMMA == MPHF_GAMMA_LINEAR) {
-        return x;
-    } else {
-        uint64_t sq = mul_hi(x, x);
-        uint64_t cube = mul_hi(sq, x);
-        uint64_t half = (sq >> 1) + (cube >> 1);
-        return half - (half >> 8) + (x >> 8);
-    }
-}
-
-// x mod S for 2 <= S < 2^32 by Barrett reduction: with M = floor(2^64 / S),
-// q = hi(x M) is floor(x / S) or one less (x M / 2^64 > x / S - 1), so
-// x - q S lies in [0, 2S) and one conditional subtraction makes it exact.
-__device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t M, uint64_t S) {
-    const uint64_t q = mul_hi(x, M);
-    uint64_t r = x - q * S;
-    if (r >= S) r -= S;
-    return r;
-}
+// The exact arithmetic of the query lives in the public device header;
+// the kernels here use it with compile-time layouts.
+using namespace mphf_dev;
 
 template <int REDUCE>
 __device__ __forceinline__ uint64_t reduce_slot(const View &v, uint64_t x) {
@@ -105,58 +84,6 @@ __device__ __forceinline__ uint64_t reduce_slot(const View &v, uint64_t x) {
     } else {
         return mod_barrett(x, v.fm, v.S);
     }
-}
-
-// Position of the i-th (0-based) set bit of a 32-bit word that has > i set bits.
-__device__ __forceinline__ uint32_t select32(uint32_t w, uint32_t i) {
-    uint32_t pos = 0, c;
-    c = __popc(w & 0xFFFFu); if (i >= c) { i -= c; w >>= 16; pos += 16; }
-    c = __popc(w & 0xFFu);   if (i >= c) { i -= c; w >>= 8;  pos += 8; }
-    c = __popc(w & 0xFu);    if (i >= c) { i -= c; w >>= 4;  pos += 4; }
-    c = __popc(w & 0x3u);    if (i >= c) { i -= c; w >>= 2;  pos += 2; }
-    c = w & 1u;              if (i >= c) { pos += 1; }
-    return pos;
-}
-
-// CacheLineEF lookup (Sec. 3.4): v = 256 (offset + select(i) - i) + low[i].
-// Line layout: bytes 0..15 the 128-bit bitmap (two little-endian words),
-// 16..19 the offset, 20..63 the low bytes.
-__device__ __forceinline__ uint32_t clef_get(const uint8_t *lines, uint32_t j) {
-    uint32_t line = j / kClefPerLine;
-    uint32_t i = j - line * kClefPerLine;
-    const uint8_t *L = lines + (uint64_t)line * 64;
-    uint4 head = __ldg(reinterpret_cast<const uint4 *>(L));        // bitmap words
-    uint32_t offset = __ldg(reinterpret_cast<const uint32_t *>(L + 16));
-    uint32_t low = __ldg(L + 20 + i);
-    uint32_t words[4] = {head.x, head.y, head.z, head.w};
-    uint32_t sel = 0, k = i;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        uint32_t c = __popc(words[q]);
-        if (k < c) { sel = 32 * q + select32(words[q], k); break; }
-        k -= c;
-    }
-    return 256u * (offset + sel - i) + low;
-}
-
-// ------------------------------------------------------------ string keys
-// Project string hash (the paper's GxHash is not specified in it):
-//   w_j = little-endian u64 of bytes [8j, 8j+8) zero-padded past len,
-//   acc = sum_j mix(w_j xor (seed + j K1)),  h = mix(acc xor len K2 xor seed),
-// mix = splitmix64 finalizer.  The sum lets every word be hashed on its own.
-__device__ __forceinline__ uint64_t str_mix(uint64_t z) {
-    z ^= z >> 30;
-    z *= 0xBF58476D1CE4E5B9ull;
-    z ^= z >> 27;
-    z *= 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return z;
-}
-constexpr uint64_t kStrK1 = 0x9E3779B97F4A7C15ull;
-constexpr uint64_t kStrK2 = 0xC2B2AE3D27D4EB4Full;
-
-__device__ __forceinline__ uint64_t str_finish(uint64_t acc, uint64_t len, uint64_t seed) {
-    return str_mix(acc ^ (len * kStrK2) ^ seed);
 }
 
 // Word j of a string that starts `start` bytes into an 8-byte-aligned buffer
@@ -170,17 +97,6 @@ __device__ __forceinline__ uint64_t load_word(const uint64_t *buf, uint32_t star
     const uint32_t rem = len - 8 * j;
     if (rem < 8) w &= (1ull << (8 * rem)) - 1;
     return w;
-}
-
-__device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uint64_t a, uint64_t len,
-                                                       uint64_t seed) {
-    uint64_t acc = 0;
-    for (uint64_t j = 0; 8 * j < len; j++) {
-        uint64_t w = 0;
-        for (uint32_t t = 0; t < 8 && 8 * j + t < len; t++) w |= (uint64_t)__ldg(bytes + a + 8 * j + t) << (8 * t);
-        acc += str_mix(w ^ (seed + j * kStrK1));
-    }
-    return str_finish(acc, len, seed);
 }
 
 constexpr int kStrStage = 2048 + 32;   // staged bytes per warp (32 strings)

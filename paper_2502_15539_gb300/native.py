@@ -63,6 +63,14 @@ class mphf_info_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class mphf_view_t(ctypes.Structure):
+    _fields_ = [("pilots", ctypes.c_void_p), ("remap", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("P", ctypes.c_uint64), ("S", ctypes.c_uint64), ("B", ctypes.c_uint64), ("C", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("barrett", ctypes.c_uint64), ("s_mask", ctypes.c_uint64),
+                ("gamma", ctypes.c_int32), ("reduce", ctypes.c_int32), ("remap_kind", ctypes.c_int32),
+                ("key_kind", ctypes.c_int32)]
+
+
 class mphf_request(ctypes.Structure):
     _fields_ = [("m", ctypes.c_void_p), ("keys_dev", ctypes.c_void_p), ("offsets_dev", ctypes.c_void_p),
                 ("count", ctypes.c_uint64), ("out_dev", ctypes.c_void_p)]
@@ -135,6 +143,7 @@ SIGNATURES = {
     "mphf_server_drain": (_i32, [_vp, _u64]),
     "mphf_server_stats": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(mphf_server_stats_t)]),
     "mphf_server_free": (None, [_vp]),
+    "mphf_device_view": (_i32, [_vp, ctypes.POINTER(mphf_view_t)]),
 }
 
 _lock = threading.Lock()
@@ -456,3 +465,10 @@ class Server:
         st = mphf_server_stats_t()
         _check(load().mphf_server_stats(self._h, int(reset), ctypes.byref(st)), "mphf_server_stats")
         return st.as_dict()
+
+
+def mphf_device_view(m: MPHF) -> mphf_view_t:
+    """The structure's device view, for kernels that include mphf_device.cuh."""
+    v = mphf_view_t()
+    _check(load().mphf_device_view(m.handle, ctypes.byref(v)), "mphf_device_view")
+    return v

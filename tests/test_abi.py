@@ -90,3 +90,19 @@ def test_header_validation_rejects_corruption(lib):
     bad[64:72] = (2).to_bytes(8, "little")                  # even mixing constant
     assert lib.mphf_deserialize(bytes(bad), len(bad), ctypes.byref(out)) == N.MPHF_ERR_FORMAT
     assert lib.mphf_deserialize(bytes(blob[:-1]), len(blob) - 1, ctypes.byref(out)) == N.MPHF_ERR_FORMAT
+
+
+def test_device_view_argument_errors(lib):
+    v = N.mphf_view_t()
+    assert lib.mphf_device_view(None, ctypes.byref(v)) == N.MPHF_ERR_ARG
+
+
+def test_device_header_compiles_in_a_caller():
+    """include/mphf_device.cuh is self-contained: a caller's translation unit
+    that includes it cross-compiles for sm_103a."""
+    from tests.device_api_common import compile_caller, nvcc
+    import tempfile
+    if nvcc() is None:
+        pytest.skip("nvcc not found")
+    with tempfile.TemporaryDirectory() as d:
+        compile_caller(os.path.join(d, "caller.o"), shared=False)
