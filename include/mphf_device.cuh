@@ -82,8 +82,9 @@ __device__ __forceinline__ uint32_t clef_get(const uint8_t *lines, uint32_t j) {
 // ------------------------------------------------------------ string keys
 // Project string hash (the paper's GxHash is not specified in it):
 //   w_j = little-endian u64 of bytes [8j, 8j+8) zero-padded past len,
-//   acc = sum_j mix(w_j xor (seed + j K1)),  h = mix(acc xor len K2 xor seed),
-// mix = splitmix64 finalizer.  The sum lets every word be hashed on its own.
+//   acc = sum_j fold(w_j xor (seed + j K1)),  h = mix(acc xor len K2 xor seed),
+// fold(x) = hi(x K3) xor lo(x K3) of the 128-bit product, mix = splitmix64
+// finalizer.  The sum lets every word be hashed on its own.
 __device__ __forceinline__ uint64_t str_mix(uint64_t z) {
     z ^= z >> 30;
     z *= 0xBF58476D1CE4E5B9ull;
@@ -94,20 +95,51 @@ __device__ __forceinline__ uint64_t str_mix(uint64_t z) {
 }
 constexpr uint64_t kStrK1 = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kStrK2 = 0xC2B2AE3D27D4EB4Full;
+constexpr uint64_t kStrK3 = 0xA173621FA8385BE3ull;
+
+__device__ __forceinline__ uint64_t str_fold(uint64_t x) { return mul_hi(x, kStrK3) ^ (x * kStrK3); }
 
 __device__ __forceinline__ uint64_t str_finish(uint64_t acc, uint64_t len, uint64_t seed) {
     return str_mix(acc ^ (len * kStrK2) ^ seed);
 }
 
+// The string hash over 32-bit little-endian words W[0], W[1], ... that hold
+// the string from bit `sh` (0, 8, 16 or 24) of W[0] on.  Word j of the
+// string is bits [64 j + sh, 64 j + sh + 64) of that sequence: two funnel
+// shifts of W[2j], W[2j+1], W[2j+2].  fetch(k) returns W[k]; it is called
+// for every k <= 2 ceil(len / 8).
+// Len is the integer type of the length and word indexes (32 bits where
+// the string is known to be short).
+template <class Fetch, class Len>
+__device__ __forceinline__ uint64_t hash_string_words(Fetch fetch, uint32_t sh, Len len, uint64_t seed) {
+    uint64_t acc = 0, tweak = seed;
+    uint32_t cur = fetch(Len(0));
+    const Len full = len >> 3;
+    for (Len j = 0; j < full; j++, tweak += kStrK1) {
+        const uint32_t m1 = fetch(2 * j + 1), m2 = fetch(2 * j + 2);
+        const uint64_t w = ((uint64_t)__funnelshift_r(m1, m2, sh) << 32) | __funnelshift_r(cur, m1, sh);
+        acc += str_fold(w ^ tweak);
+        cur = m2;
+    }
+    const uint32_t rem = (uint32_t)len & 7u;
+    if (rem) {   // the last, partial word: zero past the end of the string
+        const uint32_t m1 = fetch(2 * full + 1), m2 = fetch(2 * full + 2);
+        uint64_t w = ((uint64_t)__funnelshift_r(m1, m2, sh) << 32) | __funnelshift_r(cur, m1, sh);
+        w &= (1ull << (8 * rem)) - 1;
+        acc += str_fold(w ^ tweak);
+    }
+    return str_finish(acc, (uint64_t)len, seed);
+}
+
+// The string hash of bytes[a, a + len) in global memory, read as aligned
+// 32-bit words; words that hold no byte of the string are not read.
 __device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uint64_t a, uint64_t len,
                                                        uint64_t seed) {
-    uint64_t acc = 0;
-    for (uint64_t j = 0; 8 * j < len; j++) {
-        uint64_t w = 0;
-        for (uint32_t t = 0; t < 8 && 8 * j + t < len; t++) w |= (uint64_t)__ldg(bytes + a + 8 * j + t) << (8 * t);
-        acc += str_mix(w ^ (seed + j * kStrK1));
-    }
-    return str_finish(acc, len, seed);
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(bytes + a);
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(addr & ~(uintptr_t)3);
+    const uint64_t lead = addr & 3;   // bytes of W[0] before the string
+    return hash_string_words([&](uint64_t k) { return 4 * k < lead + len ? __ldg(w + k) : 0u; },
+                             (uint32_t)(8 * lead), len, seed);
 }
 
 // The non-minimal slot of a key hash (Eq. slot): part S + reduce(h xor hp(p), S).

@@ -73,15 +73,17 @@ void orc_part_bucket(const orc_layout *L, int gamma, uint64_t h,
 
 /* String keys.  The paper uses GxHash, which it does not define; this is the
  * project's own 64-bit string hash (parity unpinned against external values):
+ *   fold(x) = high 64 bits xor low 64 bits of the 128-bit product x * K3
+ *   w_j     = little-endian u64 of bytes [8j, 8j+8), zero-padded past len
+ *   acc     = sum_j fold(w_j xor (seed + j * K1))             (mod 2^64)
+ *   h       = mix(acc xor (len * K2) xor seed)
  *   mix(z)  = splitmix64 finalizer (Steele, Lea, Flood 2014):
  *             z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27;
  *             z *= 0x94D049BB133111EB; z ^= z>>31
- *   w_j     = little-endian u64 of bytes [8j, 8j+8), zero-padded past len
- *   acc     = sum_j mix(w_j xor (seed + j * K1))              (mod 2^64)
- *   h       = mix(acc xor (len * K2) xor seed)
- * with K1 = 0x9E3779B97F4A7C15 and K2 = 0xC2B2AE3D27D4EB4F.  The sum makes
- * the words independent of each other, so any split of the words over
- * parallel workers gives the same value. */
+ * with K1 = 0x9E3779B97F4A7C15, K2 = 0xC2B2AE3D27D4EB4F and
+ * K3 = 0xA173621FA8385BE3.  The sum makes the words independent of each
+ * other, so any split of the words over parallel workers gives the same
+ * value; one multiply per word keeps the per-word work small. */
 static uint64_t str_mix(uint64_t z) {
     z ^= z >> 30;
     z *= 0xBF58476D1CE4E5B9ull;
@@ -89,6 +91,11 @@ static uint64_t str_mix(uint64_t z) {
     z *= 0x94D049BB133111EBull;
     z ^= z >> 31;
     return z;
+}
+
+static uint64_t str_fold(uint64_t x) {
+    const unsigned __int128 p = (unsigned __int128)x * 0xA173621FA8385BE3ull;
+    return (uint64_t)(p >> 64) ^ (uint64_t)p;
 }
 
 uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed) {
@@ -102,7 +109,7 @@ uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed) {
             uint64_t byte = pos < len ? s[pos] : 0;
             w |= byte << (8 * b);
         }
-        acc += str_mix(w ^ (seed + j * K1));
+        acc += str_fold(w ^ (seed + j * K1));
     }
     return str_mix(acc ^ (len * K2) ^ seed);
 }

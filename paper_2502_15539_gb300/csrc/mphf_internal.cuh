@@ -86,19 +86,6 @@ __device__ __forceinline__ uint64_t reduce_slot(const View &v, uint64_t x) {
     }
 }
 
-// Word j of a string that starts `start` bytes into an 8-byte-aligned buffer
-// (positions inside the shared-memory stage fit 32 bits).
-__device__ __forceinline__ uint64_t load_word(const uint64_t *buf, uint32_t start, uint32_t j, uint32_t len) {
-    const uint32_t pos = start + 8 * j;
-    const uint32_t a = pos >> 3;
-    const uint32_t sh = (pos & 7) * 8;
-    uint64_t w = buf[a] >> sh;
-    if (sh) w |= buf[a + 1] << (64 - sh);
-    const uint32_t rem = len - 8 * j;
-    if (rem < 8) w &= (1ull << (8 * rem)) - 1;
-    return w;
-}
-
 constexpr int kStrStage = 2048 + 32;   // staged bytes per warp (32 strings)
 
 // Hashes the strings [w0, min(w0 + 32, count)) of a warp: lane l returns the
@@ -132,11 +119,11 @@ __device__ __forceinline__ uint64_t warp_hash_strings(const uint8_t *bytes, cons
     }
     if (lane == 0) dst[nvec] = make_uint4(0, 0, 0, 0);   // word a+1 may be read
     __syncwarp();
-    const uint64_t *buf = reinterpret_cast<const uint64_t *>(stage);
-    const uint32_t len = (uint32_t)(e - a), start = (uint32_t)(a - base);
-    uint64_t acc = 0, tweak = seed;   // tweak = seed + j K1
-    for (uint32_t j = 0; 8 * j < len; j++, tweak += kStrK1) acc += str_mix(load_word(buf, start, j, len) ^ tweak);
-    return str_finish(acc, len, seed);
+    // The stage holds every byte of the string plus at least 16 readable
+    // bytes after it, so the words past its end may be read unguarded.
+    const uint32_t start = (uint32_t)(a - base);
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (start >> 2);
+    return hash_string_words([&](uint32_t k) { return w[k]; }, 8 * (start & 3u), (uint32_t)(e - a), seed);
 }
 
 }  // namespace ptrhash

@@ -117,21 +117,53 @@ int launch_query_u64(const Header &h, const View &v, const uint64_t *keys, uint6
 }
 
 // ------------------------------------------------------------ string keys
-constexpr int kStrWarps = 8;                       // warps per block
+constexpr int kStrThreads = 256;                     // strings per tile and threads per block
+constexpr int kBlkStage = kStrThreads * 64 + 64;     // staged bytes per block
 
-// One string per lane: warp_hash_strings stages the warp's 32 contiguous
-// strings through shared memory and hashes them.
+// One string per thread.  The block's 256 contiguous strings are staged
+// through shared memory with 16-byte loads (every byte below the end of the
+// whole key buffer may be read; only the chunk crossing that end is read
+// byte by byte), then each thread hashes its string from the stage.  A
+// block whose bytes do not fit the stage hashes from global memory.
 template <int GAMMA, int REDUCE, int REMAP>
-__global__ void __launch_bounds__(kStrWarps * 32)
+__global__ void __launch_bounds__(kStrThreads)
 query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                    const uint64_t count, uint32_t *__restrict__ out) {
-    __shared__ __align__(16) uint8_t stage[kStrWarps][kStrStage];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t w0 = ((uint64_t)blockIdx.x * kStrWarps + warp) * 32;
-    if (w0 >= count) return;
-    const uint64_t h = warp_hash_strings(bytes, offsets, w0, count, stage[warp], v.seed, lane);
-    const uint64_t i = w0 + lane;
+    __shared__ __align__(16) uint8_t stage[kBlkStage];
+    const int t = threadIdx.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * kStrThreads;
+    const uint64_t last = i0 + kStrThreads < count ? i0 + kStrThreads : count;
+    const uint64_t lo = __ldg(offsets + i0), hi = __ldg(offsets + last);
+    const uint64_t i = i0 + t;
+    const uint64_t a = i < count ? __ldg(offsets + i) : hi;
+    const uint64_t e = i < count ? __ldg(offsets + i + 1) : hi;
+    const uint64_t base = lo & ~15ull;
+    const bool staged = hi - base + 32 <= (uint64_t)kBlkStage;   // + one zeroed chunk
+    if (staged) {
+        const uint64_t end_all = last < count ? __ldg(offsets + count) : hi;
+        const uint32_t nvec = (uint32_t)((hi - base + 15) / 16);
+        uint4 *dst = reinterpret_cast<uint4 *>(stage);
+        for (uint32_t q = t; q < nvec; q += kStrThreads) {
+            const uint64_t c0 = base + 16ull * q;
+            if (c0 + 16 <= end_all) {
+                dst[q] = __ldcs(reinterpret_cast<const uint4 *>(bytes + c0));
+            } else {   // the chunk crossing the end of the key buffer
+                uint8_t *d8 = stage + 16 * q;
+                for (int k = 0; k < 16; k++) d8[k] = c0 + k < hi ? __ldg(bytes + c0 + k) : 0;
+            }
+        }
+        if (t == 0) dst[nvec] = make_uint4(0, 0, 0, 0);   // words past the last string may be read
+        __syncthreads();
+    }
     if (i >= count) return;
+    uint64_t h;
+    if (staged) {
+        const uint32_t st = (uint32_t)(a - base);
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (st >> 2);
+        h = hash_string_words([&](uint32_t k) { return w[k]; }, 8 * (st & 3u), (uint32_t)(e - a), v.seed);
+    } else {
+        h = hash_string_global(bytes, a, e - a, v.seed);
+    }
     uint64_t part;
     const uint64_t b = bucket_of<GAMMA>(v, h, part);
     const uint32_t p = __ldg(v.pilots + b);
@@ -141,14 +173,13 @@ query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64
 template <int GAMMA, int REDUCE, int REMAP>
 static int launch_bytes_t(const View &v, const uint8_t *bytes, const uint64_t *offsets, uint64_t count,
                           uint32_t *out, cudaStream_t s) {
-    const uint64_t per_block = kStrWarps * 32;
-    const uint64_t blocks = (count + per_block - 1) / per_block;
+    const uint64_t blocks = (count + kStrThreads - 1) / kStrThreads;
     if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
     if ((uintptr_t)bytes % 16) {
         set_error("byte keys need a 16-byte aligned buffer");
         return MPHF_ERR_ARG;
     }
-    query_bytes_kernel<GAMMA, REDUCE, REMAP><<<(unsigned)blocks, per_block, 0, s>>>(v, bytes, offsets, count, out);
+    query_bytes_kernel<GAMMA, REDUCE, REMAP><<<(unsigned)blocks, kStrThreads, 0, s>>>(v, bytes, offsets, count, out);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "query_bytes launch");

@@ -175,6 +175,34 @@ def test_query_bytes_long_and_empty_strings():
     assert np.array_equal(got, ref.query_bytes(data, off))
 
 
+def test_query_bytes_mixed_lengths_and_unstaged_blocks():
+    """Lengths 0..200 B (every word-count bin, including the > 14 words one),
+    a few 3000-B strings that push their 256-string block off the shared-memory
+    stage, and a ragged last block."""
+    N = need_gpu()
+    rng = np.random.default_rng(4)
+    n = 5000 + 77
+    lens = rng.integers(0, 201, size=n)
+    lens[rng.choice(n, size=6, replace=False)] = 3000
+    pieces = []
+    for i, l in enumerate(lens):
+        p = rng.integers(0, 256, size=int(l), dtype=np.uint8)
+        if l >= 3:   # distinct strings: the index in the first bytes
+            p[:3] = [i & 0xFF, (i >> 8) & 0xFF, 0x7F]
+        pieces.append(p)
+    keep = [i for i, l in enumerate(lens) if l >= 3] + [int(np.argmin(lens))]
+    pieces = [pieces[i] for i in keep]
+    off = np.zeros(len(pieces) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([len(p) for p in pieces])
+    data = np.concatenate(pieces)
+    ref = O.OracleMPHF.build_bytes(data, off)
+    m = N.mphf_deserialize(ref.serialize())
+    got = u32(N.mphf_query_bytes(m, torch.from_numpy(data).cuda(),
+                                 torch.from_numpy(off.view(np.int64)).cuda()))
+    assert np.array_equal(got, ref.query_bytes(data, off))
+    assert np.array_equal(np.sort(got), np.arange(len(pieces), dtype=np.uint32))
+
+
 def test_gather_probe_reads_the_table():
     N = need_gpu()
     keys = W.u64_keys(5000, 7)
