@@ -67,6 +67,11 @@ typedef struct {
     uint64_t slots_override;  /* 0: the parameter rule picks S; else forced S */
     int32_t  max_reseeds;     /* extra attempts with seed+1, seed+2, ...      */
     uint32_t evict_mult;      /* a part fails after evict_mult * S evictions  */
+    uint64_t shard_keys;      /* build in shards of whole parts holding about
+                                 this many keys each (in-memory sharding,
+                                 Appendix B); 0: automatic, from the free
+                                 device memory.  The structure is the same
+                                 for every value.                             */
 } mphf_params;
 
 /* Fills *p with the Default parameters.  Returns MPHF_ERR_ARG for NULL. */

@@ -32,6 +32,7 @@ constexpr int kPendingCap = 8192;       // deferred or evicted buckets waiting f
 constexpr int kSetSize = 4096;          // slot set for self-collision checks
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kMaxSlots = 1ull << 20;   // bitvector in shared memory
+constexpr uint64_t kMaxShardKeys = 0xFFFFFFFFull - 1;   // bucket starts are 32-bit
 
 enum : uint32_t { kPartOk = 0, kPartNoPilot = 1, kPartEvictCap = 2, kPartBigBucket = 3, kPartPendingFull = 4 };
 
@@ -48,23 +49,65 @@ __device__ __forceinline__ uint64_t global_bucket(uint64_t h, uint64_t P, uint64
     return part * B + mul_hi(B, bucket_fn<GAMMA>(P * h));
 }
 
-// bstart[b] = index of the first sorted hash in global bucket b (b <= P*B).
+// The n sorted hashes all lie in global buckets [gb_lo, gb_hi); bstart[b -
+// gb_lo] = index of the first of them in bucket b, for gb_lo <= b <= gb_hi.
 template <int GAMMA>
 __global__ void bucket_bounds_kernel(const uint64_t *__restrict__ sorted, uint64_t n, uint64_t P, uint64_t B,
-                                     uint32_t *__restrict__ bstart, uint32_t *__restrict__ dup) {
+                                     uint64_t gb_lo, uint64_t gb_hi, uint32_t *__restrict__ bstart,
+                                     uint32_t *__restrict__ dup) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t hi_b = i < n ? global_bucket<GAMMA>(sorted[i], P, B) : P * B;
-        const uint64_t lo_b = i > 0 ? global_bucket<GAMMA>(sorted[i - 1], P, B) + 1 : 0;
-        for (uint64_t b = lo_b; b <= hi_b; b++) bstart[b] = (uint32_t)i;
+        const uint64_t hi_b = i < n ? global_bucket<GAMMA>(sorted[i], P, B) : gb_hi;
+        const uint64_t lo_b = i > 0 ? global_bucket<GAMMA>(sorted[i - 1], P, B) + 1 : gb_lo;
+        for (uint64_t b = lo_b; b <= hi_b; b++) bstart[b - gb_lo] = (uint32_t)i;
         if (i > 0 && i < n && sorted[i] == sorted[i - 1]) *dup = 1;
     }
 }
 
-__global__ void part_size_kernel(const uint32_t *__restrict__ bstart, uint64_t P, uint64_t B, uint64_t S,
+// Parts [0, nparts) of the bstart array (relative to its first part).
+__global__ void part_size_kernel(const uint32_t *__restrict__ bstart, uint64_t nparts, uint64_t B, uint64_t S,
                                  uint32_t *__restrict__ overfull) {
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x)
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nparts; p += (uint64_t)gridDim.x * blockDim.x)
         if (bstart[(p + 1) * B] - bstart[p * B] > S) *overfull = 1;
+}
+
+// One shard of the keys: the hashes of the keys whose part lies in
+// [part_lo, part_hi), appended in any order (they are sorted next).  At
+// most `cap` are stored; more raise *overflow (some part then holds more
+// than S keys).  h = C k for u64 keys, the string hash for byte keys.
+__global__ void shard_hash_kernel(int key_kind, const void *__restrict__ keys, const uint64_t *__restrict__ offsets,
+                                  uint64_t n, uint64_t C, uint64_t seed, uint64_t P, uint64_t part_lo,
+                                  uint64_t part_hi, uint64_t *__restrict__ out, uint64_t cap,
+                                  unsigned long long *__restrict__ count, uint32_t *__restrict__ overflow) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // Every lane of a warp runs the same number of iterations.
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (uint64_t w = first; w < n; w += stride) {
+        const uint64_t i = w + lane;
+        uint64_t h = 0;
+        bool keep = false;
+        if (i < n) {
+            if (key_kind == MPHF_KEY_U64) {
+                h = C * __ldg(static_cast<const uint64_t *>(keys) + i);
+            } else {
+                const uint64_t a = __ldg(offsets + i), e = __ldg(offsets + i + 1);
+                h = hash_string_global(static_cast<const uint8_t *>(keys), a, e - a, seed);
+            }
+            const uint64_t part = mul_hi(P, h);
+            keep = part >= part_lo && part < part_hi;
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+        if (!m) continue;
+        unsigned long long base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+        if (keep) {
+            const uint64_t j = base + __popc(m & ((1u << lane) - 1));
+            if (j < cap) out[j] = h;
+            else *overflow = 1;
+        }
+    }
 }
 
 // ------------------------------------------------------ step 4: the search
@@ -80,6 +123,10 @@ struct SearchArgs {
     unsigned long long *evictions;
     uint32_t *next_part;
     uint64_t P, S, B, C, seed, fm, s_mask, evict_cap;
+    // Parts [part_begin, part_end) are searched; `sorted` holds their hashes
+    // and bstart[b - bbase] indexes it for their global buckets b, with
+    // bbase = part_begin * B (one shard of the parts, or all of them).
+    uint64_t part_begin, part_end, bbase;
 };
 
 template <int REDUCE>
@@ -190,7 +237,7 @@ __device__ int greedy_large(const SearchArgs &a, const SearchShared &sh, int s, 
 }
 
 __device__ __forceinline__ uint64_t bucket_size(const SearchArgs &a, uint64_t gb0, uint32_t b) {
-    return a.bstart[gb0 + b + 1] - a.bstart[gb0 + b];
+    return a.bstart[gb0 - a.bbase + b + 1] - a.bstart[gb0 - a.bbase + b];
 }
 
 // Least weighted collisions (Sec. 3.2): cost = sum over the bucket's keys
@@ -308,7 +355,7 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
             if (lane == 0) sh.pend[best_i] = sh.pend[np - 1];
             np--;
             __syncwarp();
-            const uint64_t kbase = a.bstart[gb0 + b];
+            const uint64_t kbase = a.bstart[gb0 - a.bbase + b];
             myh = lane < s ? a.sorted[kbase + lane] : 0;
             if (s > kSmallBucket) {
                 for (int j = lane; j < s; j += 32) sh.hcache[j] = a.sorted[kbase + j];
@@ -349,7 +396,7 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
                 const uint32_t oe = owner[sl];
                 const uint32_t o = oe & kOwnerMask;
                 const uint64_t os = oe >> kOwnerShift;
-                const uint64_t ob = a.bstart[gb0 + o];
+                const uint64_t ob = a.bstart[gb0 - a.bbase + o];
                 const uint64_t ohp = a.C * ((uint64_t)a.pilots[gb0 + o] ^ a.seed);
                 for (uint64_t k = lane; k < os; k += 32) {
                     const uint32_t osl = slot_in_part<REDUCE>(a, a.sorted[ob + k] ^ ohp);
@@ -510,15 +557,15 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchA
     for (;;) {
         if (tid == 0) { s_part = atomicAdd(a.next_part, 1u); s_flag = 0; }
         __syncthreads();
-        const uint64_t p = s_part;
-        if (p >= a.P) break;
+        const uint64_t p = a.part_begin + s_part;
+        if (p >= a.part_end) break;
         const uint64_t gb0 = p * a.B;
         // 1. Bucket sizes, counted per warp over its own range of buckets.
         for (uint64_t w = tid; w < kPrepWords; w += blockDim.x) cnt[w] = 0;
         __syncthreads();
         const uint64_t lo = warp * chunk, hi = (lo + chunk < a.B ? lo + chunk : a.B);
         for (uint64_t b = lo + lane; b < hi; b += 32) {
-            const uint32_t z = a.bstart[gb0 + b + 1] - a.bstart[gb0 + b];
+            const uint32_t z = a.bstart[gb0 - a.bbase + b + 1] - a.bstart[gb0 - a.bbase + b];
             if (z > (uint32_t)kMaxBucket) s_flag = 1;
             else if (z) atomicAdd(&cnt[warp * (kMaxBucket + 1) + z], 1u);
         }
@@ -560,7 +607,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchA
         // 3. Stable scatter of the descriptors, every warp over its range.
         for (uint64_t base = lo; base < hi; base += 32) {
             const uint64_t b = base + lane;
-            const uint32_t z = b < hi ? a.bstart[gb0 + b + 1] - a.bstart[gb0 + b] : 0;
+            const uint32_t z = b < hi ? a.bstart[gb0 - a.bbase + b + 1] - a.bstart[gb0 - a.bbase + b] : 0;
             const unsigned peers = __match_any_sync(0xFFFFFFFFu, z);
             const unsigned rank = __popc(peers & ((1u << lane) - 1));
             uint32_t pos = 0;
@@ -578,7 +625,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchA
         for (uint32_t pos = tid; pos < nb; pos += blockDim.x) {
             const uint64_t d = order[pos];
             const uint32_t b = (uint32_t)d, z = (uint32_t)(d >> 32) & 0xFFFu;
-            const uint64_t koff = d >> 44, src = a.bstart[gb0 + b];
+            const uint64_t koff = d >> 44, src = a.bstart[gb0 - a.bbase + b];
             for (uint32_t k = 0; k < z; k++) ohash[koff + k] = a.sorted[src + k];
         }
         const uint32_t n_large = sh.hist[kSmallBucket];   // positions of buckets > kSmallBucket keys
@@ -747,11 +794,30 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     CK(cudaEventRecord(t0, s));
 
     const uint64_t total = P * S, nbkt = P * B, words = (total + 31) / 32;
-    const unsigned search_grid = (unsigned)(P < (uint64_t)sms ? P : (uint64_t)sms);
+    // Shards of whole parts (the in-memory sharding of Appendix B): every
+    // shard hashes all keys and keeps, sorts and searches only the hashes of
+    // its parts, so the working memory follows the shard, not n.  A part's
+    // search sees only its own keys, so the structure does not depend on the
+    // sharding.
+    uint64_t shard_keys = prm.shard_keys;
+    if (shard_keys == 0) {   // automatic: a quarter of the free memory at 24 bytes per key
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        shard_keys = free_b / 4 / 24;
+    }
+    uint64_t parts_per_shard = (uint64_t)((double)shard_keys * (double)P / (double)n);
+    if (parts_per_shard > kMaxShardKeys / S) parts_per_shard = kMaxShardKeys / S;   // 32-bit bucket starts
+    if (parts_per_shard < 1) parts_per_shard = 1;
+    if (parts_per_shard > P) parts_per_shard = P;
+    const uint64_t shards = (P + parts_per_shard - 1) / parts_per_shard;
+    const uint64_t max_parts = (P + shards - 1) / shards;    // shard i: parts [P i / shards, P (i+1) / shards)
+    const uint64_t cap = shards == 1 ? n : max_parts * S;    // hashes a valid shard can hold
+    if (cap > kMaxShardKeys) { set_error("%llu keys in one shard", (unsigned long long)cap); return MPHF_ERR_CAPACITY; }
+    const unsigned search_grid = (unsigned)(max_parts < (uint64_t)sms ? max_parts : (uint64_t)sms);
     DevBuf hash, sorted, bstart, pilots, taken, owner, order, ohash, status, flags, cub_tmp;
-    CK(hash.alloc(n * 8));
-    CK(sorted.alloc(n * 8));
-    CK(bstart.alloc((nbkt + 1) * 4));
+    CK(hash.alloc(cap * 8));
+    CK(sorted.alloc(cap * 8));
+    CK(bstart.alloc((max_parts * B + 1) * 4));
     CK(pilots.alloc((nbkt + 63) & ~63ull));
     CK(taken.alloc((words + 1) * 4));
     CK(owner.alloc((uint64_t)search_grid * S * 4));
@@ -760,9 +826,10 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     CK(status.alloc(P * 4));
     CK(flags.alloc(64));
     size_t sort_tmp = 0;
-    CK(cub::DeviceRadixSort::SortKeys(nullptr, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), n, 0, 64, s));
+    CK(cub::DeviceRadixSort::SortKeys(nullptr, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), cap, 0, 64, s));
     CK(cub_tmp.alloc(sort_tmp));
-    uint32_t *d_flags = flags.as<uint32_t>();   // [0] dup, [1] overfull, [2] next part, [3] span, [4..5] evictions
+    // [0] dup, [1] overfull, [2] next part, [3] span, [4..5] evictions, [6] shard overflow, [8..9] shard count
+    uint32_t *d_flags = flags.as<uint32_t>();
 
     const size_t smem = search_smem_bytes(S);
     Header h;
@@ -775,62 +842,91 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     for (int attempt = 0; attempt < attempts && !built; attempt++) {
         const uint64_t seed = prm.seed + (uint64_t)attempt;
         h.seed = seed;
-        CK(cudaMemsetAsync(d_flags, 0, 64, s));
-        rc = launch_hash_keys(key_kind, keys, offsets, n, prm.C, seed, hash.as<uint64_t>(), sms, s);
-        if (rc) return rc;
-        CK(cub::DeviceRadixSort::SortKeys(cub_tmp.p, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), n, 0, 64, s));
-        count_launch(4);
-        if (prm.gamma == MPHF_GAMMA_CUBIC)
-            bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted.as<uint64_t>(), n, P, B, bstart.as<uint32_t>(), d_flags);
-        else
-            bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted.as<uint64_t>(), n, P, B, bstart.as<uint32_t>(), d_flags);
-        part_size_kernel<<<grid_for(P, sms), 256, 0, s>>>(bstart.as<uint32_t>(), P, B, S, d_flags + 1);
-        count_launch(2);
-        CK(cudaGetLastError());
-        uint32_t hf[2];
-        CK(cudaMemcpyAsync(hf, d_flags, 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (hf[0]) {
-            last_fail = MPHF_ERR_DUP_KEYS;
-            set_error("equal key hashes (duplicate keys)");
-            if (key_kind == MPHF_KEY_U64) return MPHF_ERR_DUP_KEYS;   // h = C k: duplicates for sure
-            continue;
-        }
-        if (hf[1]) {
-            last_fail = MPHF_ERR_OVERFULL;
-            set_error("a part holds more than S=%llu keys", (unsigned long long)S);
-            if (key_kind == MPHF_KEY_U64) return MPHF_ERR_OVERFULL;   // the seed does not move u64 keys
-            continue;
-        }
         CK(cudaMemsetAsync(taken.p, 0, (words + 1) * 4, s));
         CK(cudaMemsetAsync(pilots.p, 0, nbkt, s));
-        SearchArgs a;
-        a.sorted = sorted.as<uint64_t>(); a.bstart = bstart.as<uint32_t>(); a.pilots = pilots.as<uint8_t>();
-        a.taken = taken.as<uint32_t>(); a.owner_scratch = owner.as<uint32_t>(); a.order_scratch = order.as<uint64_t>();
-        a.ohash_scratch = ohash.as<uint64_t>();
-        a.status = status.as<uint32_t>();
-        a.evictions = reinterpret_cast<unsigned long long *>(d_flags + 4);
-        a.next_part = d_flags + 2;
-        a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;
-        a.fm = reduce == kReduceMod ? barrett_constant(S) : 0;
-        a.evict_cap = (uint64_t)prm.evict_mult * S;
-        CK(reduce == kReducePow2 ? launch_search<kReducePow2>(a, search_grid, smem, s)
-                                 : launch_search<kReduceMod>(a, search_grid, smem, s));
-        std::vector<uint32_t> st(P);
-        unsigned long long ev = 0;
-        CK(cudaMemcpyAsync(st.data(), status.p, P * 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&ev, d_flags + 4, 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        evictions_total += ev;
-        uint64_t failed = 0, first_bad = 0;
-        for (uint64_t p = 0; p < P; p++) if (st[p] != kPartOk) { if (!failed) first_bad = p; failed++; }
-        if (failed) {
-            last_fail = MPHF_ERR_BUILD_FAILED;
-            set_error("%llu part(s) failed (first: part %llu, status %u) with seed %llu", (unsigned long long)failed,
-                      (unsigned long long)first_bad, st[first_bad], (unsigned long long)seed);
-            continue;
+        bool ok = true;
+        for (uint64_t sh = 0; sh < shards && ok; sh++) {
+            const uint64_t p_lo = P * sh / shards, p_hi = P * (sh + 1) / shards;
+            CK(cudaMemsetAsync(d_flags, 0, 64, s));
+            uint64_t m = n;
+            if (shards == 1) {
+                rc = launch_hash_keys(key_kind, keys, offsets, n, prm.C, seed, hash.as<uint64_t>(), sms, s);
+                if (rc) return rc;
+            } else {
+                shard_hash_kernel<<<grid_for(n, sms), 256, 0, s>>>(
+                    key_kind, keys, offsets, n, prm.C, seed, P, p_lo, p_hi, hash.as<uint64_t>(), cap,
+                    reinterpret_cast<unsigned long long *>(d_flags + 8), d_flags + 6);
+                count_launch();
+                CK(cudaGetLastError());
+                uint32_t fl[4];
+                CK(cudaMemcpyAsync(fl, d_flags + 6, 16, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                m = (uint64_t)fl[2] | ((uint64_t)fl[3] << 32);
+                if (fl[0]) m = cap + 1;   // too many keys for the shard's parts: reported below as overfull
+            }
+            uint32_t hf[2] = {0, 0};
+            if (m <= cap) {
+                CK(cub::DeviceRadixSort::SortKeys(cub_tmp.p, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), m, 0, 64, s));
+                count_launch(4);
+                const uint64_t gb_lo = p_lo * B, gb_hi = p_hi * B;
+                if (prm.gamma == MPHF_GAMMA_CUBIC)
+                    bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(m + 1, sms), 256, 0, s>>>(
+                        sorted.as<uint64_t>(), m, P, B, gb_lo, gb_hi, bstart.as<uint32_t>(), d_flags);
+                else
+                    bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(m + 1, sms), 256, 0, s>>>(
+                        sorted.as<uint64_t>(), m, P, B, gb_lo, gb_hi, bstart.as<uint32_t>(), d_flags);
+                part_size_kernel<<<grid_for(p_hi - p_lo, sms), 256, 0, s>>>(bstart.as<uint32_t>(), p_hi - p_lo, B, S, d_flags + 1);
+                count_launch(2);
+                CK(cudaGetLastError());
+                CK(cudaMemcpyAsync(hf, d_flags, 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+            } else {
+                hf[1] = 1;
+            }
+            if (hf[0]) {
+                last_fail = MPHF_ERR_DUP_KEYS;
+                set_error("equal key hashes (duplicate keys)");
+                if (key_kind == MPHF_KEY_U64) return MPHF_ERR_DUP_KEYS;   // h = C k: duplicates for sure
+                ok = false;
+                break;
+            }
+            if (hf[1]) {
+                last_fail = MPHF_ERR_OVERFULL;
+                set_error("a part holds more than S=%llu keys", (unsigned long long)S);
+                if (key_kind == MPHF_KEY_U64) return MPHF_ERR_OVERFULL;   // the seed does not move u64 keys
+                ok = false;
+                break;
+            }
+            SearchArgs a;
+            a.sorted = sorted.as<uint64_t>(); a.bstart = bstart.as<uint32_t>(); a.pilots = pilots.as<uint8_t>();
+            a.taken = taken.as<uint32_t>(); a.owner_scratch = owner.as<uint32_t>(); a.order_scratch = order.as<uint64_t>();
+            a.ohash_scratch = ohash.as<uint64_t>();
+            a.status = status.as<uint32_t>();
+            a.evictions = reinterpret_cast<unsigned long long *>(d_flags + 4);
+            a.next_part = d_flags + 2;
+            a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;
+            a.fm = reduce == kReduceMod ? barrett_constant(S) : 0;
+            a.evict_cap = (uint64_t)prm.evict_mult * S;
+            a.part_begin = p_lo; a.part_end = p_hi; a.bbase = p_lo * B;
+            const unsigned grid = (unsigned)(p_hi - p_lo < (uint64_t)search_grid ? p_hi - p_lo : (uint64_t)search_grid);
+            CK(reduce == kReducePow2 ? launch_search<kReducePow2>(a, grid, smem, s)
+                                     : launch_search<kReduceMod>(a, grid, smem, s));
+            std::vector<uint32_t> st(p_hi - p_lo);
+            unsigned long long ev = 0;
+            CK(cudaMemcpyAsync(st.data(), status.as<uint32_t>() + p_lo, (p_hi - p_lo) * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&ev, d_flags + 4, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            evictions_total += ev;
+            uint64_t failed = 0, first_bad = 0;
+            for (uint64_t q = 0; q < p_hi - p_lo; q++) if (st[q] != kPartOk) { if (!failed) first_bad = p_lo + q; failed++; }
+            if (failed) {
+                last_fail = MPHF_ERR_BUILD_FAILED;
+                set_error("%llu part(s) failed (first: part %llu, status %u) with seed %llu", (unsigned long long)failed,
+                          (unsigned long long)first_bad, st[first_bad - p_lo], (unsigned long long)seed);
+                ok = false;
+            }
         }
-        built = true;
+        built = ok;
     }
     if (!built) return last_fail;
 
@@ -1032,9 +1128,9 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
         CK(cub::DeviceRadixSort::SortKeys(sort_buf, sort_tmp, hash, sorted, n, 0, 64, s));
         count_launch(4);
         if (prm.gamma == MPHF_GAMMA_CUBIC)
-            bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, bstart, flags);
+            bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, 0, P * B, bstart, flags);
         else
-            bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, bstart, flags);
+            bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, 0, P * B, bstart, flags);
         part_size_kernel<<<grid_for(P, sms), 256, 0, s>>>(bstart, P, B, S, flags + 1);
         count_launch(2);
         CK(cudaGetLastError());
@@ -1050,6 +1146,7 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
         a.order_scratch = order; a.ohash_scratch = ohash; a.status = status;
         a.evictions = reinterpret_cast<unsigned long long *>(flags + 4);
         a.next_part = flags + 2;
+        a.part_begin = 0; a.part_end = P; a.bbase = 0;
         a.P = P; a.S = S; a.B = B; a.C = prm.C; a.seed = seed; a.s_mask = S - 1;
         a.fm = reduce == kReduceMod ? barrett_constant(S) : 0;
         a.evict_cap = (uint64_t)prm.evict_mult * S;

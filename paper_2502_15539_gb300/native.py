@@ -47,7 +47,7 @@ class mphf_params(ctypes.Structure):
                 ("gamma", ctypes.c_int32), ("remap", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("C", ctypes.c_uint64),
                 ("slots_override", ctypes.c_uint64), ("max_reseeds", ctypes.c_int32),
-                ("evict_mult", ctypes.c_uint32)]
+                ("evict_mult", ctypes.c_uint32), ("shard_keys", ctypes.c_uint64)]
 
 
 class mphf_info_t(ctypes.Structure):

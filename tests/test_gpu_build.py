@@ -106,3 +106,32 @@ def test_gpu_build_duplicate_strings_rejected():
     with pytest.raises(N.MphfError) as e:
         N.mphf_build(data.cuda(), N.mphf_default_params(max_reseeds=2), offsets=off.cuda())
     assert e.value.code == N.MPHF_ERR_DUP_KEYS
+
+
+# (n, shard_keys): 1e6 keys are P = 4 parts, 3e6 are 6, 2e7 are 39; the shard
+# sizes give one part per shard, uneven shards, and many shards.
+SHARD_CASES = [(10**6, 300_000), (10**6, 600_000), (3 * 10**6, 1_400_000), (2 * 10**7, 3_000_000)]
+
+
+@pytest.mark.parametrize("n,shard_keys", SHARD_CASES)
+def test_sharded_build_is_identical(n, shard_keys):
+    """In-memory sharding by part ranges (Appendix B, Sharding) changes only
+    how the build walks the keys: the structure is the same, byte for byte."""
+    N = need_gpu()
+    keys = W.u64_keys(n, 9).cuda()
+    whole = N.mphf_serialize(N.mphf_build(keys))
+    m = N.mphf_build(keys, N.mphf_default_params(shard_keys=shard_keys))
+    assert N.mphf_serialize(m) == whole
+    check_bijection(N, m, keys, n)
+
+
+def test_sharded_string_build_is_identical():
+    N = need_gpu()
+    n = 300_000
+    data, off = W.strings(torch.arange(n), seed=7)
+    data, off = data.cuda(), off.cuda()
+    whole = N.mphf_serialize(N.mphf_build(data, offsets=off))
+    m = N.mphf_build(data, N.mphf_default_params(shard_keys=40_000), offsets=off)   # P = 3: three shards
+    assert N.mphf_serialize(m) == whole
+    got = u32(N.mphf_query_bytes(m, data, off))
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
