@@ -87,7 +87,8 @@ typedef struct {
                                                  1 = x mod S (Sec. 3.1)      */
     uint64_t remap_len;       /* P*S - n entries of the remap table F          */
     uint64_t pilot_bytes;     /* P*B                                           */
-    uint64_t remap_bytes;     /* CacheLineEF: 64 per 44 entries; Vec: 4 each    */
+    uint64_t remap_bytes;     /* CacheLineEF: 64 per 44 entries; Vec: 4 each
+                                 (8 once n > 2^32)                             */
     double   bits_per_key;    /* 8 (pilot_bytes + remap_bytes) / n              */
     uint64_t evictions;       /* hash-evict evictions of the build (0 if loaded)*/
     double   build_ms;        /* device time of mphf_build (0 if loaded)        */
@@ -101,7 +102,9 @@ typedef struct {
  *             MPHF_KEY_BYTES: keys_dev = packed bytes (device pointer);
  *             offsets_dev = n+1 non-decreasing uint64_t (device), key i being
  *             bytes [offsets[i], offsets[i+1]).
- *   n         1 <= n < 2^32.
+ *   n         1 <= n <= 2^40 (CacheLineEF stores values below 2^40).
+ *             Beyond 2^32 keys the values need the _wide queries, and the
+ *             build runs in shards of whole parts (see shard_keys).
  * Runs on `stream` and returns once the structure is complete (it
  * synchronizes that stream).  Temporary device memory is allocated and freed
  * inside.  Errors: MPHF_ERR_ARG, MPHF_ERR_DUP_KEYS (equal u64 keys, or equal
@@ -118,7 +121,8 @@ int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
  * keys_dev: m uint64_t (device, 8-byte aligned; 16-byte alignment takes the
  * vectorized path); out_dev: m uint32_t (device, 4-byte aligned).  Keys that
  * are not members give a deterministic value in [0, n).  m = 0 is a no-op.
- * Asynchronous on `stream`.  Errors: MPHF_ERR_ARG, MPHF_ERR_CUDA (launch). */
+ * Needs n <= 2^32 (values fit 32 bits).  Asynchronous on `stream`.  Errors:
+ * MPHF_ERR_ARG, MPHF_ERR_CUDA (launch). */
 int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
                    uint32_t *out_dev, void *stream);
 
@@ -128,6 +132,15 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
 int mphf_query_bytes(const mphf_t *m, const uint8_t *bytes_dev,
                      const uint64_t *offsets_dev, uint64_t count,
                      uint32_t *out_dev, void *stream);
+
+/* The same queries with uint64_t results, for any structure (needed once
+ * n > 2^32; for smaller n the values equal the 32-bit ones).  out_dev: m
+ * uint64_t (device, 8-byte aligned).  Other arguments and errors as above. */
+int mphf_query_u64_wide(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
+                        uint64_t *out_dev, void *stream);
+int mphf_query_bytes_wide(const mphf_t *m, const uint8_t *bytes_dev,
+                          const uint64_t *offsets_dev, uint64_t count,
+                          uint64_t *out_dev, void *stream);
 
 /* Perfect (non-minimal) hash: slot(k_i) in [0, P*S) without the remap
  * (Sec. 3.1 Eq. slot; Table remap "Query PHF").  Same arguments as

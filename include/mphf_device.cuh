@@ -79,6 +79,26 @@ __device__ __forceinline__ uint32_t clef_get(const uint8_t *lines, uint32_t j) {
     return 256u * (offset + sel - i) + low;
 }
 
+// The same lookup with 64-bit arithmetic, for structures of more than 2^32
+// keys (values up to 2^40, remap positions past 2^32).
+__device__ __forceinline__ uint64_t clef_get64(const uint8_t *lines, uint64_t j) {
+    const uint64_t line = j / 44u;
+    const uint32_t i = (uint32_t)(j - line * 44u);
+    const uint8_t *L = lines + line * 64;
+    const uint4 head = __ldg(reinterpret_cast<const uint4 *>(L));
+    const uint64_t offset = __ldg(reinterpret_cast<const uint32_t *>(L + 16));
+    const uint64_t low = __ldg(L + 20 + i);
+    const uint32_t words[4] = {head.x, head.y, head.z, head.w};
+    uint32_t sel = 0, k = i;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const uint32_t c = __popc(words[q]);
+        if (k < c) { sel = 32 * q + select32(words[q], k); break; }
+        k -= c;
+    }
+    return 256ull * (offset + sel - i) + low;
+}
+
 // ------------------------------------------------------------ string keys
 // Project string hash (the paper's GxHash is not specified in it):
 //   w_j = little-endian u64 of bytes [8j, 8j+8) zero-padded past len,
@@ -154,6 +174,7 @@ __device__ __forceinline__ uint64_t slot_hash(const mphf_view_t &v, uint64_t h) 
 }
 
 // The MPHF value of a key hash: the slot, or its remap entry when >= n.
+// The 32-bit forms need n <= 2^32; the _wide forms take any structure.
 __device__ __forceinline__ uint32_t eval_hash(const mphf_view_t &v, uint64_t h) {
     const uint64_t s = slot_hash(v, h);
     if (s < v.n) return (uint32_t)s;
@@ -162,12 +183,28 @@ __device__ __forceinline__ uint32_t eval_hash(const mphf_view_t &v, uint64_t h) 
     return __ldg(static_cast<const uint32_t *>(v.remap) + j);
 }
 
+__device__ __forceinline__ uint64_t eval_hash_wide(const mphf_view_t &v, uint64_t h) {
+    const uint64_t s = slot_hash(v, h);
+    if (s < v.n) return s;
+    const uint64_t j = s - v.n;
+    if (v.remap_kind == MPHF_REMAP_CLEF) return clef_get64(static_cast<const uint8_t *>(v.remap), j);
+    if (v.n > (1ull << 32)) return __ldg(static_cast<const unsigned long long *>(v.remap) + j);
+    return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+}
+
 // A u64 key (structures built with MPHF_KEY_U64).
 __device__ __forceinline__ uint32_t eval_u64(const mphf_view_t &v, uint64_t key) { return eval_hash(v, v.C * key); }
+
+__device__ __forceinline__ uint64_t eval_u64_wide(const mphf_view_t &v, uint64_t key) {
+    return eval_hash_wide(v, v.C * key);
+}
 
 // A byte-string key (structures built with MPHF_KEY_BYTES).
 __device__ __forceinline__ uint32_t eval_bytes(const mphf_view_t &v, const uint8_t *s, uint64_t len) {
     return eval_hash(v, hash_string_global(s, 0, len, v.seed));
+}
+__device__ __forceinline__ uint64_t eval_bytes_wide(const mphf_view_t &v, const uint8_t *s, uint64_t len) {
+    return eval_hash_wide(v, hash_string_global(s, 0, len, v.seed));
 }
 
 }  // namespace mphf_dev

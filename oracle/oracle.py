@@ -113,7 +113,7 @@ def lib():
             L.orc_build_bytes.argtypes = [vp, vp, u64, ctypes.POINTER(Params), ctypes.POINTER(vp)]
             L.orc_free.restype = None; L.orc_free.argtypes = [vp]
             L.orc_slot_of_hash.restype = u64; L.orc_slot_of_hash.argtypes = [vp, u64]
-            L.orc_query_hash.restype = ctypes.c_uint32; L.orc_query_hash.argtypes = [vp, u64]
+            L.orc_query_hash.restype = u64; L.orc_query_hash.argtypes = [vp, u64]
             L.orc_query_u64_many.restype = None
             L.orc_query_u64_many.argtypes = [vp, vp, u64, vp, i32]
             L.orc_query_bytes_many.restype = None
@@ -282,18 +282,26 @@ class OracleMPHF:
         ptr = lib().orc_pilots(self._h)
         return np.ctypeslib.as_array(ptr, shape=(L.P * L.B,)).copy()
 
+    @property
+    def wide(self) -> bool:
+        """Values pass 32 bits (n > 2^32): results come as uint64, else uint32."""
+        return self.layout.n > (1 << 32)
+
+    def _values(self, out: np.ndarray) -> np.ndarray:
+        return out if self.wide else out.astype(np.uint32)
+
     def remap_values(self) -> np.ndarray:
         m = lib().orc_remap_len(self._h)
-        out = np.zeros(max(m, 1), dtype=np.uint32)
+        out = np.zeros(max(m, 1), dtype=np.uint64)
         lib().orc_remap_values(self._h, _ptr(out))
-        return out[:m]
+        return self._values(out[:m])
 
     # -- queries, one key at a time
     def query_u64(self, keys: np.ndarray, threads: int = 1) -> np.ndarray:
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
-        out = np.zeros(max(len(keys), 1), dtype=np.uint32)
+        out = np.zeros(max(len(keys), 1), dtype=np.uint64)
         lib().orc_query_u64_many(self._h, _ptr(keys), len(keys), _ptr(out), threads)
-        return out[: len(keys)]
+        return self._values(out[: len(keys)])
 
     def query_bytes(self, data: np.ndarray, offsets: np.ndarray, threads: int = 1) -> np.ndarray:
         data = np.ascontiguousarray(data, dtype=np.uint8)
@@ -301,9 +309,9 @@ class OracleMPHF:
             data = np.zeros(1, np.uint8)
         offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         cnt = len(offsets) - 1
-        out = np.zeros(max(cnt, 1), dtype=np.uint32)
+        out = np.zeros(max(cnt, 1), dtype=np.uint64)
         lib().orc_query_bytes_many(self._h, _ptr(data), _ptr(offsets), cnt, _ptr(out), threads)
-        return out[:cnt]
+        return self._values(out[:cnt])
 
     def slots_u64(self, keys: np.ndarray) -> np.ndarray:
         """PHF (non-minimal) values: the slot before remapping."""

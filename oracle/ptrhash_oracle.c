@@ -130,7 +130,7 @@ static int is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
  * slots_override != 0 forces S (reduce then follows S being a power of 2). */
 int orc_layout_for(uint64_t n, double lambda, double alpha,
                    uint64_t slots_override, orc_layout *out) {
-    if (n == 0 || n > 0xFFFFFFFFull || !(lambda > 0.0) || !(alpha > 0.0) || alpha > 1.0)
+    if (n == 0 || n > ORC_MAX_KEYS || !(lambda > 0.0) || !(alpha > 0.0) || alpha > 1.0)
         return ORC_ERR_ARG;
     memset(out, 0, sizeof(*out));
     out->n = n;
@@ -164,7 +164,7 @@ int orc_layout_for(uint64_t n, double lambda, double alpha,
     if (P < 1) P = 1;
     uint64_t B = (uint64_t)ceil(alpha * (double)S / lambda);
     if (B < 1) B = 1;
-    if (P * S < n || P * S > 0xFFFFFFFFull) return ORC_ERR_ARG;
+    if (P * S < n || P * S - n >= ORC_MAX_KEYS || S > 0xFFFFFFFFull) return ORC_ERR_ARG;
     out->P = P;
     out->S = S;
     out->B = B;
@@ -263,10 +263,10 @@ static uint64_t remap_get(const orc_mphf *m, uint64_t j) {
 }
 
 /* A slot >= n is replaced by F[slot - n] (Sec. 3.4, "Remapping"). */
-uint32_t orc_query_hash(const orc_mphf *m, uint64_t h) {
+uint64_t orc_query_hash(const orc_mphf *m, uint64_t h) {
     uint64_t s = orc_slot_of_hash(m, h);
-    if (s < m->L.n) return (uint32_t)s;
-    return (uint32_t)remap_get(m, s - m->L.n);
+    if (s < m->L.n) return s;
+    return remap_get(m, s - m->L.n);
 }
 
 typedef struct {
@@ -274,7 +274,7 @@ typedef struct {
     const uint64_t *keys;
     const uint8_t *bytes;
     const uint64_t *offsets;
-    uint32_t *out;
+    uint64_t *out;
     uint64_t lo, hi;
 } query_job;
 
@@ -311,13 +311,13 @@ static void run_split(void *(*fn)(void *), query_job base, uint64_t cnt, int thr
 }
 
 void orc_query_u64_many(const orc_mphf *m, const uint64_t *keys, uint64_t cnt,
-                        uint32_t *out, int threads) {
+                        uint64_t *out, int threads) {
     query_job J = {m, keys, NULL, NULL, out, 0, 0};
     run_split(query_u64_worker, J, cnt, threads);
 }
 
 void orc_query_bytes_many(const orc_mphf *m, const uint8_t *bytes,
-                          const uint64_t *offsets, uint64_t cnt, uint32_t *out,
+                          const uint64_t *offsets, uint64_t cnt, uint64_t *out,
                           int threads) {
     query_job J = {m, NULL, bytes, offsets, out, 0, 0};
     run_split(query_bytes_worker, J, cnt, threads);
@@ -626,9 +626,9 @@ static int build_remap(orc_mphf *m, const uint8_t *taken, int want_clef) {
         m->clef_lines = 0;
     }
     if (rc == ORC_OK && m->remap == ORC_REMAP_VEC) {
-        m->vec = (uint32_t *)malloc((m->remap_len ? m->remap_len : 1) * sizeof(uint32_t));
+        m->vec = (uint64_t *)malloc((m->remap_len ? m->remap_len : 1) * sizeof(uint64_t));
         if (!m->vec) { free(F); return ORC_ERR_OOM; }
-        for (uint64_t j = 0; j < m->remap_len; j++) m->vec[j] = (uint32_t)F[j];
+        for (uint64_t j = 0; j < m->remap_len; j++) m->vec[j] = F[j];
     }
     free(F);
     return rc;
@@ -741,12 +741,15 @@ void orc_free(orc_mphf *m) {
  *  56 u64 B | 64 u64 C | 72 u64 seed | 80 u64 remap_len | 88 u64 remap_bytes
  *  96 f64 lambda | 104 f64 alpha | 112 u64 pilot_bytes (=P*B) | 120 u64 0
  * then the pilots (P*B bytes) zero-padded to a multiple of 64, then the
- * remap payload (CacheLineEF lines of 64 bytes, or u32 entries). */
+ * remap payload (CacheLineEF lines of 64 bytes, or plain entries: u32, or
+ * u64 when n > 2^32 and the values no longer fit 32 bits). */
+
+static uint64_t vec_width(uint64_t n) { return n > (1ull << 32) ? 8 : 4; }
 
 static uint64_t pad64(uint64_t v) { return (v + 63) & ~63ull; }
 
 static uint64_t remap_bytes_of(const orc_mphf *m) {
-    return m->remap == ORC_REMAP_CLEF ? 64 * m->clef_lines : 4 * m->remap_len;
+    return m->remap == ORC_REMAP_CLEF ? 64 * m->clef_lines : vec_width(m->L.n) * m->remap_len;
 }
 
 uint64_t orc_serialized_size(const orc_mphf *m) {
@@ -779,7 +782,8 @@ int orc_serialize(const orc_mphf *m, uint8_t *buf, uint64_t cap) {
     memcpy(buf + 128, m->pilots, m->L.P * m->L.B);
     uint8_t *rp = buf + 128 + pad64(m->L.P * m->L.B);
     if (m->remap == ORC_REMAP_CLEF) memcpy(rp, m->clef, 64 * m->clef_lines);
-    else for (uint64_t j = 0; j < m->remap_len; j++) put_u32(rp + 4 * j, m->vec[j]);
+    else if (vec_width(m->L.n) == 8) for (uint64_t j = 0; j < m->remap_len; j++) put_u64(rp + 8 * j, m->vec[j]);
+    else for (uint64_t j = 0; j < m->remap_len; j++) put_u32(rp + 4 * j, (uint32_t)m->vec[j]);
     return ORC_OK;
 }
 
@@ -807,13 +811,14 @@ int orc_deserialize(const uint8_t *buf, uint64_t len, orc_mphf **out) {
               (m->remap != ORC_REMAP_CLEF && m->remap != ORC_REMAP_VEC) ||
               (m->L.reduce != ORC_REDUCE_POW2 && m->L.reduce != ORC_REDUCE_MOD) ||
               m->L.n == 0 || m->L.P == 0 || m->L.S == 0 || m->L.B == 0 ||
+              m->L.n > ORC_MAX_KEYS || m->L.S > 0xFFFFFFFFull ||
               pb != m->L.P * m->L.B || m->L.P * m->L.S < m->L.n ||
               m->remap_len != m->L.P * m->L.S - m->L.n ||
               (m->L.reduce == ORC_REDUCE_POW2 && !is_pow2(m->L.S));
     if (!bad) {
         uint64_t want = m->remap == ORC_REMAP_CLEF
                             ? 64 * ((m->remap_len + ORC_CLEF_PER_LINE - 1) / ORC_CLEF_PER_LINE)
-                            : 4 * m->remap_len;
+                            : vec_width(m->L.n) * m->remap_len;
         bad = rbytes != want || len < 128 + pad64(pb) + rbytes;
     }
     if (bad) { orc_free(m); return ORC_ERR_FORMAT; }
@@ -827,9 +832,10 @@ int orc_deserialize(const uint8_t *buf, uint64_t len, orc_mphf **out) {
         if (!m->clef) { orc_free(m); return ORC_ERR_OOM; }
         memcpy(m->clef, rp, rbytes);
     } else {
-        m->vec = (uint32_t *)malloc((m->remap_len ? m->remap_len : 1) * 4);
+        m->vec = (uint64_t *)malloc((m->remap_len ? m->remap_len : 1) * 8);
         if (!m->vec) { orc_free(m); return ORC_ERR_OOM; }
-        for (uint64_t j = 0; j < m->remap_len; j++) m->vec[j] = get_u32(rp + 4 * j);
+        if (vec_width(m->L.n) == 8) for (uint64_t j = 0; j < m->remap_len; j++) m->vec[j] = get_u64(rp + 8 * j);
+        else for (uint64_t j = 0; j < m->remap_len; j++) m->vec[j] = get_u32(rp + 4 * j);
     }
     *out = m;
     return ORC_OK;
@@ -842,8 +848,8 @@ int orc_deserialize(const uint8_t *buf, uint64_t len, orc_mphf **out) {
 void orc_get_layout(const orc_mphf *m, orc_layout *L) { *L = m->L; }
 const uint8_t *orc_pilots(const orc_mphf *m) { return m->pilots; }
 uint64_t orc_remap_len(const orc_mphf *m) { return m->remap_len; }
-void orc_remap_values(const orc_mphf *m, uint32_t *out) {
-    for (uint64_t j = 0; j < m->remap_len; j++) out[j] = (uint32_t)remap_get(m, j);
+void orc_remap_values(const orc_mphf *m, uint64_t *out) {
+    for (uint64_t j = 0; j < m->remap_len; j++) out[j] = remap_get(m, j);
 }
 uint64_t orc_seed(const orc_mphf *m) { return m->seed; }
 int orc_remap_kind(const orc_mphf *m) { return m->remap; }

@@ -38,7 +38,7 @@ extern "C" {
 #define ORC_GAMMA_CUBIC  3 /* gamma_3, the default      (Sec. 3.3)        */
 
 #define ORC_REMAP_CLEF 0   /* CacheLineEF               (Sec. 3.4, Eq. clef) */
-#define ORC_REMAP_VEC  1   /* plain u32 array F         (Sec. 3.4)        */
+#define ORC_REMAP_VEC  1   /* plain array F: u32, u64 once n > 2^32 (Sec. 3.4) */
 
 #define ORC_REDUCE_POW2 0  /* reduce(x,S) = hi(C x) mod S, S = 2^k (Sec. 3.1) */
 #define ORC_REDUCE_MOD  1  /* reduce(x,S) = x mod S, S not 2^k  (Sec. 3.1)  */
@@ -47,6 +47,10 @@ extern "C" {
 #define ORC_KEY_BYTES 1
 
 #define ORC_CLEF_PER_LINE 44
+
+/* CacheLineEF keeps values below 2^40 (a 32-bit offset in units of 256),
+ * which bounds n; values pass 32 bits once n > 2^32. */
+#define ORC_MAX_KEYS (1ull << 40)
 
 /* Layout chosen by the parameter rule (Sec. 3.1 "Parameter values"). */
 typedef struct {
@@ -82,7 +86,7 @@ typedef struct {
     uint8_t *pilots;        /* P*B bytes                                   */
     uint64_t remap_len;     /* P*S - n entries of F                        */
     uint8_t *clef;          /* ceil(remap_len/44) lines of 64 bytes        */
-    uint32_t *vec;          /* remap_len entries (ORC_REMAP_VEC)           */
+    uint64_t *vec;          /* remap_len entries (ORC_REMAP_VEC)           */
     uint64_t clef_lines;
 } orc_mphf;
 
@@ -118,11 +122,11 @@ void orc_free(orc_mphf *m);
 
 /* ---- query (one key at a time) ---- */
 uint64_t orc_slot_of_hash(const orc_mphf *m, uint64_t h);
-uint32_t orc_query_hash(const orc_mphf *m, uint64_t h);
+uint64_t orc_query_hash(const orc_mphf *m, uint64_t h);
 void orc_query_u64_many(const orc_mphf *m, const uint64_t *keys, uint64_t cnt,
-                        uint32_t *out, int threads);
+                        uint64_t *out, int threads);
 void orc_query_bytes_many(const orc_mphf *m, const uint8_t *bytes,
-                          const uint64_t *offsets, uint64_t cnt, uint32_t *out,
+                          const uint64_t *offsets, uint64_t cnt, uint64_t *out,
                           int threads);
 /* PHF (non-minimal) query: the slot before remapping. */
 void orc_slot_u64_many(const orc_mphf *m, const uint64_t *keys, uint64_t cnt,
@@ -137,7 +141,7 @@ int orc_deserialize(const uint8_t *buf, uint64_t len, orc_mphf **out);
 void orc_get_layout(const orc_mphf *m, orc_layout *L);
 const uint8_t *orc_pilots(const orc_mphf *m);
 uint64_t orc_remap_len(const orc_mphf *m);
-void orc_remap_values(const orc_mphf *m, uint32_t *out); /* decoded F */
+void orc_remap_values(const orc_mphf *m, uint64_t *out); /* decoded F */
 uint64_t orc_seed(const orc_mphf *m);
 int orc_remap_kind(const orc_mphf *m);
 int orc_gamma_kind(const orc_mphf *m);

@@ -56,7 +56,7 @@ static bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
 // of two.  A forced S keeps P = ceil(n / (alpha S)).
 int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_override,
                   uint64_t *P_out, uint64_t *S_out, uint64_t *B_out, int *reduce_out) {
-    if (n == 0 || n > 0xFFFFFFFFull || !(lambda > 0.0) || !(alpha > 0.0) || alpha > 1.0) {
+    if (n == 0 || n > kMaxKeys || !(lambda > 0.0) || !(alpha > 0.0) || alpha > 1.0) {
         set_error("invalid n=%llu, lambda=%g or alpha=%g", (unsigned long long)n, lambda, alpha);
         return MPHF_ERR_ARG;
     }
@@ -87,7 +87,7 @@ int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_overri
     if (P == 0) P = 1;
     uint64_t B = (uint64_t)ceil(alpha * (double)S / lambda);
     if (B == 0) B = 1;
-    if (P * S < n || P * S > 0xFFFFFFFFull || B > 0xFFFFFFFEull) {
+    if (P * S < n || P * S - n >= kMaxKeys || S > 0xFFFFFFFFull || B > 0xFFFFFFFEull) {
         set_error("layout out of range: P=%llu S=%llu B=%llu", (unsigned long long)P,
                   (unsigned long long)S, (unsigned long long)B);
         return MPHF_ERR_ARG;
@@ -161,7 +161,8 @@ int mphf_layout(const mphf_params *params, uint64_t n, mphf_info_t *out) {
     out->C = params->C; out->seed = params->seed; out->gamma = params->gamma; out->remap = params->remap;
     out->remap_len = P * S - n;
     out->pilot_bytes = P * B;
-    out->remap_bytes = params->remap == MPHF_REMAP_VEC ? 4 * out->remap_len : 64 * clef_lines_for(out->remap_len);
+    out->remap_bytes = params->remap == MPHF_REMAP_VEC ? vec_entry_bytes(n) * out->remap_len
+                                                       : 64 * clef_lines_for(out->remap_len);
     out->bits_per_key = 8.0 * (double)(out->pilot_bytes + out->remap_bytes) / (double)n;
     return MPHF_OK;
 }
@@ -245,14 +246,15 @@ static int parse_serialized(const uint8_t *b, size_t len, Header *out, uint64_t 
                (h.gamma != MPHF_GAMMA_LINEAR && h.gamma != MPHF_GAMMA_CUBIC) ||
                (h.remap != MPHF_REMAP_CLEF && h.remap != MPHF_REMAP_VEC) ||
                (h.reduce != kReducePow2 && h.reduce != kReduceMod) ||
-               h.n == 0 || h.n > 0xFFFFFFFFull || h.P == 0 || h.S == 0 || h.B == 0 ||
+               h.n == 0 || h.n > kMaxKeys || h.P == 0 || h.S == 0 || h.B == 0 ||
                h.S > 0xFFFFFFFFull || h.P > 0xFFFFFFFFull || h.B > 0xFFFFFFFFull ||
-               pb != h.P * h.B || h.P * h.S < h.n || h.P * h.S > 0xFFFFFFFFull ||
+               pb != h.P * h.B || h.P * h.S < h.n || h.P * h.S - h.n >= kMaxKeys ||
                h.remap_len != h.P * h.S - h.n || (h.C & 1) == 0 ||
                (h.reduce == kReducePow2 && !is_pow2(h.S)) ||
                (h.reduce == kReduceMod && is_pow2(h.S));
     if (!bad) {
-        uint64_t want = h.remap == MPHF_REMAP_CLEF ? 64 * clef_lines_for(h.remap_len) : 4 * h.remap_len;
+        uint64_t want = h.remap == MPHF_REMAP_CLEF ? 64 * clef_lines_for(h.remap_len)
+                                                   : vec_entry_bytes(h.n) * h.remap_len;
         bad = h.remap_bytes != want || len < 128 + round64(pb) + h.remap_bytes;
     }
     if (bad) { set_error("inconsistent header fields"); return MPHF_ERR_FORMAT; }
@@ -264,12 +266,13 @@ static int parse_serialized(const uint8_t *b, size_t len, Header *out, uint64_t 
 namespace ptrhash {
 
 // Device bytes a serialized structure needs in an arena (256-byte aligned parts).
-int serialized_device_bytes(const void *blob, size_t len, uint64_t *bytes) {
+int serialized_device_bytes(const void *blob, size_t len, uint64_t *bytes, uint64_t *n) {
     Header h;
     uint64_t pb = 0;
     int rc = parse_serialized((const uint8_t *)blob, len, &h, &pb);
     if (rc) return rc;
     *bytes = ((pb + 255) & ~255ull) + ((h.remap_bytes + 255) & ~255ull);
+    if (n) *n = h.n;
     return MPHF_OK;
 }
 
@@ -404,8 +407,22 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, ui
         return MPHF_ERR_ARG;
     }
     if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    if (wide_values(m->hdr.n)) { set_error("n > 2^32: values need the _wide query"); return MPHF_ERR_ARG; }
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
     return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, false, (cudaStream_t)stream);
+}
+
+int mphf_query_u64_wide(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint64_t *out_dev,
+                        void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    if (!keys_dev || !out_dev || ((uintptr_t)keys_dev & 7) || ((uintptr_t)out_dev & 7)) {
+        set_error("keys and out must be 8-byte aligned device pointers");
+        return MPHF_ERR_ARG;
+    }
+    if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    return launch_query_u64_wide(m->hdr, v, keys_dev, count, out_dev, (cudaStream_t)stream);
 }
 
 int mphf_query_u64_phf(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
@@ -417,6 +434,7 @@ int mphf_query_u64_phf(const mphf_t *m, const uint64_t *keys_dev, uint64_t count
         return MPHF_ERR_ARG;
     }
     if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    if (m->hdr.P * m->hdr.S > (1ull << 32)) { set_error("P S > 2^32: slots do not fit 32 bits"); return MPHF_ERR_ARG; }
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
     return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, true, (cudaStream_t)stream);
 }
@@ -430,8 +448,22 @@ int mphf_query_bytes(const mphf_t *m, const uint8_t *bytes_dev, const uint64_t *
         return MPHF_ERR_ARG;
     }
     if (m->hdr.key_kind != MPHF_KEY_BYTES) { set_error("structure was built for u64 keys"); return MPHF_ERR_ARG; }
+    if (wide_values(m->hdr.n)) { set_error("n > 2^32: values need the _wide query"); return MPHF_ERR_ARG; }
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
     return launch_query_bytes(m->hdr, v, bytes_dev, offsets_dev, count, out_dev, (cudaStream_t)stream);
+}
+
+int mphf_query_bytes_wide(const mphf_t *m, const uint8_t *bytes_dev, const uint64_t *offsets_dev,
+                          uint64_t count, uint64_t *out_dev, void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    if (!bytes_dev || !offsets_dev || !out_dev || ((uintptr_t)offsets_dev & 7) || ((uintptr_t)out_dev & 7)) {
+        set_error("bad pointers for byte-key query");
+        return MPHF_ERR_ARG;
+    }
+    if (m->hdr.key_kind != MPHF_KEY_BYTES) { set_error("structure was built for u64 keys"); return MPHF_ERR_ARG; }
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    return launch_query_bytes_wide(m->hdr, v, bytes_dev, offsets_dev, count, out_dev, (cudaStream_t)stream);
 }
 
 // Host-buffer query: chunk c uses buffer set c % 2.  The copy in of chunk c
@@ -445,6 +477,7 @@ int mphf_query_u64_host(mphf_t *m, const uint64_t *keys_host, uint64_t count, ui
     if (count == 0) return MPHF_OK;
     if (!keys_host || !out_host) { set_error("NULL host buffer"); return MPHF_ERR_ARG; }
     if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    if (wide_values(m->hdr.n)) { set_error("n > 2^32: values need the _wide query"); return MPHF_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
     // Page-locked host buffers are mapped into the device address space: the
     // kernel then reads the keys and writes the results across the host link

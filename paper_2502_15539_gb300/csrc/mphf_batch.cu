@@ -241,6 +241,7 @@ static int stage_requests(mphf_batch *b, uint8_t *hb, const mphf_request *reqs, 
             return MPHF_ERR_ARG;
         }
         const Header &h = handle_header(r.m);
+        if (wide_values(h.n)) { set_error("request %u: n > 2^32 (32-bit results)", i); return MPHF_ERR_ARG; }
         if ((h.key_kind == MPHF_KEY_BYTES) != (r.offsets_dev != nullptr)) {
             set_error("request %u: offsets must be given exactly for byte-key structures", i);
             return MPHF_ERR_ARG;

@@ -32,7 +32,7 @@ constexpr int kPendingCap = 8192;       // deferred or evicted buckets waiting f
 constexpr int kSetSize = 4096;          // slot set for self-collision checks
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kMaxSlots = 1ull << 20;   // bitvector in shared memory
-constexpr uint64_t kMaxShardKeys = 0xFFFFFFFFull - 1;   // bucket starts are 32-bit
+constexpr uint64_t kMaxShardKeys = (1ull << 31) - 1;   // 32-bit bucket starts, int-sized sorts
 
 enum : uint32_t { kPartOk = 0, kPartNoPilot = 1, kPartEvictCap = 2, kPartBigBucket = 3, kPartPendingFull = 4 };
 
@@ -692,15 +692,15 @@ __global__ void remap_count_kernel(const uint32_t *__restrict__ taken, uint64_t 
     }
 }
 
-// L[r] = position of the r-th free slot below n.
+// L[r] = position of the r-th free slot below n (positions may pass 2^32).
 __global__ void free_list_kernel(const uint32_t *__restrict__ taken, uint64_t words, uint64_t n,
-                                 const uint32_t *__restrict__ free_rank, uint32_t *__restrict__ L) {
+                                 const uint32_t *__restrict__ free_rank, uint64_t *__restrict__ L) {
     for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t m = ~taken[w] & low_mask(w, n);
         uint32_t r = free_rank[w];
         while (m) {
             const int bpos = __ffs(m) - 1;
-            L[r++] = (uint32_t)(32 * w + bpos);
+            L[r++] = 32 * w + bpos;
             m &= m - 1;
         }
     }
@@ -709,8 +709,8 @@ __global__ void free_list_kernel(const uint32_t *__restrict__ taken, uint64_t wo
 // F[j] = L[t - 1] with t the number of taken slots in [n, n + j]; entries
 // before the first taken slot take L[0]; all zero when R = 0.
 __global__ void remap_values_kernel(const uint32_t *__restrict__ taken, const uint32_t *__restrict__ high_rank,
-                                    const uint32_t *__restrict__ L, uint64_t n, uint64_t total, uint64_t R,
-                                    uint32_t *__restrict__ F) {
+                                    const uint64_t *__restrict__ L, uint64_t n, uint64_t total, uint64_t R,
+                                    uint64_t *__restrict__ F) {
     const uint64_t len = total - n;
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t q = n + j, w = q >> 5;
@@ -720,26 +720,33 @@ __global__ void remap_values_kernel(const uint32_t *__restrict__ taken, const ui
     }
 }
 
-// One CacheLineEF line per thread (Sec. 3.4, Eq. clef).
-__global__ void clef_encode_kernel(const uint32_t *__restrict__ F, uint64_t len, uint64_t lines,
+// One CacheLineEF line per thread (Sec. 3.4, Eq. clef).  Values are below
+// 2^40 (the 32-bit offset counts units of 256).
+__global__ void clef_encode_kernel(const uint64_t *__restrict__ F, uint64_t len, uint64_t lines,
                                    uint8_t *__restrict__ out, uint32_t *__restrict__ span_fail) {
     for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < lines; c += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i0 = c * kClefPerLine;
-        const uint32_t v0 = F[i0];
-        const uint32_t offset = v0 >> 8;
+        const uint64_t v0 = F[i0];
+        const uint64_t offset = v0 >> 8;
         uint32_t words[4] = {0, 0, 0, 0};
         uint8_t *line = out + 64 * c;
         for (int i = 0; i < kClefPerLine; i++) {
             const uint64_t idx = i0 + i < len ? i0 + i : len - 1;
-            const uint32_t v = F[idx];
-            const uint32_t bit = i + ((v >> 8) - offset);
+            const uint64_t v = F[idx];
+            const uint64_t bit = i + ((v >> 8) - offset);
             if (bit >= 128) { *span_fail = 1; break; }
             words[bit >> 5] |= 1u << (bit & 31);
             line[20 + i] = (uint8_t)v;
         }
         reinterpret_cast<uint4 *>(line)[0] = make_uint4(words[0], words[1], words[2], words[3]);
-        reinterpret_cast<uint32_t *>(line)[4] = offset;
+        reinterpret_cast<uint32_t *>(line)[4] = (uint32_t)offset;
     }
+}
+
+// The plain remap array: u32 entries, or u64 once values reach 2^32.
+__global__ void narrow_kernel(const uint64_t *__restrict__ F, uint64_t len, uint32_t *__restrict__ out) {
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (uint64_t)gridDim.x * blockDim.x)
+        out[j] = (uint32_t)F[j];
 }
 
 // ------------------------------------------------------------ orchestration
@@ -806,7 +813,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
         shard_keys = free_b / 4 / 24;
     }
     uint64_t parts_per_shard = (uint64_t)((double)shard_keys * (double)P / (double)n);
-    if (parts_per_shard > kMaxShardKeys / S) parts_per_shard = kMaxShardKeys / S;   // 32-bit bucket starts
+    if (parts_per_shard > kMaxShardKeys / S) parts_per_shard = kMaxShardKeys / S;
     if (parts_per_shard < 1) parts_per_shard = 1;
     if (parts_per_shard > P) parts_per_shard = P;
     const uint64_t shards = (P + parts_per_shard - 1) / parts_per_shard;
@@ -959,17 +966,17 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
                   (unsigned long long)R_high);
         return MPHF_ERR_BUILD_FAILED;
     }
-    CK(L.alloc(R_low * 4));
-    CK(F.alloc(len * 4));
-    free_list_kernel<<<grid_for(words, sms), 256, 0, s>>>(taken.as<uint32_t>(), words, n, free_rank.as<uint32_t>(), L.as<uint32_t>());
-    remap_values_kernel<<<grid_for(len, sms), 256, 0, s>>>(taken.as<uint32_t>(), high_rank.as<uint32_t>(), L.as<uint32_t>(),
-                                                           n, total, R_low, F.as<uint32_t>());
+    CK(L.alloc(R_low * 8));
+    CK(F.alloc(len * 8));
+    free_list_kernel<<<grid_for(words, sms), 256, 0, s>>>(taken.as<uint32_t>(), words, n, free_rank.as<uint32_t>(), L.as<uint64_t>());
+    remap_values_kernel<<<grid_for(len, sms), 256, 0, s>>>(taken.as<uint32_t>(), high_rank.as<uint32_t>(), L.as<uint64_t>(),
+                                                           n, total, R_low, F.as<uint64_t>());
     count_launch(2);
     int remap_kind = prm.remap;
     if (remap_kind == MPHF_REMAP_CLEF && len > 0) {
         const uint64_t lines = clef_lines_for(len);
         CK(remap.alloc(lines * 64));
-        clef_encode_kernel<<<grid_for(lines, sms), 256, 0, s>>>(F.as<uint32_t>(), len, lines, remap.as<uint8_t>(), d_flags + 3);
+        clef_encode_kernel<<<grid_for(lines, sms), 256, 0, s>>>(F.as<uint64_t>(), len, lines, remap.as<uint8_t>(), d_flags + 3);
         count_launch();
         uint32_t span_fail = 0;
         CK(cudaMemcpyAsync(&span_fail, d_flags + 3, 4, cudaMemcpyDeviceToHost, s));
@@ -984,8 +991,15 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
         h.remap_bytes = 0;
     }
     if (remap_kind == MPHF_REMAP_VEC) {
-        remap.p = F.release();
-        h.remap_bytes = len * 4;
+        const uint64_t width = vec_entry_bytes(n);
+        if (width == 8) {
+            remap.p = F.release();
+        } else {
+            CK(remap.alloc(len * 4));
+            narrow_kernel<<<grid_for(len, sms), 256, 0, s>>>(F.as<uint64_t>(), len, remap.as<uint32_t>());
+            count_launch();
+        }
+        h.remap_bytes = len * width;
     }
     h.remap = remap_kind;
     CK(cudaGetLastError());
@@ -1103,9 +1117,10 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
     uint32_t *flags = c.take<uint32_t>(64);
     uint32_t *free_cnt = c.take<uint32_t>(words * 4), *high_cnt = c.take<uint32_t>(words * 4);
     uint32_t *free_rank = c.take<uint32_t>((words + 1) * 4), *high_rank = c.take<uint32_t>((words + 1) * 4);
-    uint32_t *L = c.take<uint32_t>(len * 4), *F = c.take<uint32_t>(len * 4);
+    uint64_t *L = c.take<uint64_t>(len * 8), *F = c.take<uint64_t>(len * 8);
+    uint32_t *F32 = c.take<uint32_t>(len * 4);
     uint8_t *lines_buf = c.take<uint8_t>(lines * 64);
-    if (!lines_buf || !F || !L || !high_rank || !free_rank || !high_cnt || !free_cnt || !flags || !status || !order ||
+    if (!lines_buf || !F32 || !F || !L || !high_rank || !free_rank || !high_cnt || !free_cnt || !flags || !status || !order ||
         !ohash || !owner || !taken || !pilots || !bstart || !scan_buf || !sort_buf || !sorted || !hash) {
         set_error("this layout needs more than the %llu-byte scratch array", (unsigned long long)kNoAllocScratchBytes);
         return MPHF_ERR_CAPACITY;
@@ -1180,8 +1195,10 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
     free_list_kernel<<<grid_for(words, sms), 256, 0, s>>>(taken, words, n, free_rank, L);
     remap_values_kernel<<<grid_for(len, sms), 256, 0, s>>>(taken, high_rank, L, n, total, R, F);
     count_launch(2);
+    narrow_kernel<<<grid_for(len, sms), 256, 0, s>>>(F, len, F32);   // n < 2^32 here: u32 entries
+    count_launch();
     h.remap = prm.remap;
-    const uint8_t *remap_src = reinterpret_cast<const uint8_t *>(F);
+    const uint8_t *remap_src = reinterpret_cast<const uint8_t *>(F32);
     h.remap_bytes = len * 4;
     if (prm.remap == MPHF_REMAP_CLEF) {
         h.remap_bytes = lines * 64;
@@ -1192,7 +1209,7 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
             uint32_t span_fail = 0;
             CK(cudaMemcpyAsync(&span_fail, flags + 3, 4, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            if (span_fail) { h.remap = MPHF_REMAP_VEC; h.remap_bytes = len * 4; remap_src = reinterpret_cast<const uint8_t *>(F); }
+            if (span_fail) { h.remap = MPHF_REMAP_VEC; h.remap_bytes = len * 4; remap_src = reinterpret_cast<const uint8_t *>(F32); }
         }
     }
     CK(cudaGetLastError());

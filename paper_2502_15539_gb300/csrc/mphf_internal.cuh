@@ -49,6 +49,13 @@ int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_overri
 uint64_t barrett_constant(uint64_t S);
 uint64_t clef_lines_for(uint64_t remap_len);
 
+// Keys a structure may hold: CacheLineEF stores values below 2^40 (a 32-bit
+// offset in units of 256).  Values pass 32 bits once n > 2^32; the plain
+// remap array then holds u64 entries, and the results need 64-bit outputs.
+constexpr uint64_t kMaxKeys = 1ull << 40;
+inline bool wide_values(uint64_t n) { return n > (1ull << 32); }
+inline uint64_t vec_entry_bytes(uint64_t n) { return wide_values(n) ? 8 : 4; }
+
 View make_view(const Header &h, const uint8_t *pilots, const void *remap);
 
 // Query launchers (mphf_query.cu).
@@ -56,6 +63,10 @@ int launch_query_u64(const Header &h, const View &v, const uint64_t *keys, uint6
                      uint32_t *out, bool phf, cudaStream_t s);
 int launch_query_bytes(const Header &h, const View &v, const uint8_t *bytes,
                        const uint64_t *offsets, uint64_t count, uint32_t *out, cudaStream_t s);
+int launch_query_u64_wide(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint64_t *out,
+                          cudaStream_t s);
+int launch_query_bytes_wide(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
+                            uint64_t count, uint64_t *out, cudaStream_t s);
 
 // Key hashes for the builder (mphf_query.cu).
 int launch_hash_keys(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t C,

@@ -34,6 +34,46 @@ __device__ __forceinline__ uint32_t slot_value(const View &v, uint64_t h, uint64
     else return __ldg(static_cast<const uint32_t *>(v.remap) + j);
 }
 
+// 64-bit results (any structure; needed once n > 2^32).  The plain remap
+// array holds u64 entries exactly when n > 2^32.
+template <int REDUCE, int REMAP>
+__device__ __forceinline__ uint64_t slot_value_wide(const View &v, uint64_t h, uint64_t part, uint32_t pilot) {
+    const uint64_t x = h ^ (v.C * ((uint64_t)pilot ^ v.seed));
+    const uint64_t s = part * v.S + reduce_slot<REDUCE>(v, x);
+    if (s < v.n) return s;
+    const uint64_t j = s - v.n;
+    if constexpr (REMAP == kRemapClef) return clef_get64(static_cast<const uint8_t *>(v.remap), j);
+    else if (v.n > (1ull << 32)) return __ldg(static_cast<const unsigned long long *>(v.remap) + j);
+    else return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+}
+
+template <int GAMMA, int REDUCE, int REMAP>
+__global__ void __launch_bounds__(kThreads)
+query_u64_wide_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
+                      uint64_t *__restrict__ out) {
+    constexpr int K = kKeysPerThread;
+    const uint64_t tile = (uint64_t)blockIdx.x * (kThreads * K);
+    uint64_t h[K], part[K], b[K];
+    uint32_t p[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+        h[q] = v.C * (i < count ? __ldcs(keys + i) : 0ull);
+        b[q] = bucket_of<GAMMA>(v, h[q], part[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+        p[q] = i < count ? __ldg(v.pilots + b[q]) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+        if (i < count) __stcs(reinterpret_cast<unsigned long long *>(out) + i,
+                              (unsigned long long)slot_value_wide<REDUCE, REMAP>(v, h[q], part[q], p[q]));
+    }
+}
+
 // VEC: keys 16-byte and out 8-byte aligned; pairs of keys per load / store.
 template <int GAMMA, int REDUCE, int REMAP, bool PHF, bool VEC>
 __global__ void __launch_bounds__(kThreads)
@@ -106,6 +146,31 @@ static int dispatch_remap(const Header &h, const View &v, const uint64_t *keys, 
     return launch_u64_t<GAMMA, REDUCE, kRemapClef, false>(v, keys, count, out, s);
 }
 
+template <int GAMMA, int REDUCE, int REMAP>
+static int launch_u64_wide_t(const View &v, const uint64_t *keys, uint64_t count, uint64_t *out, cudaStream_t s) {
+    const uint64_t per_block = (uint64_t)kThreads * kKeysPerThread;
+    const uint64_t blocks = (count + per_block - 1) / per_block;
+    if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
+    query_u64_wide_kernel<GAMMA, REDUCE, REMAP><<<(unsigned)blocks, kThreads, 0, s>>>(v, keys, count, out);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "query_u64_wide launch");
+}
+
+int launch_query_u64_wide(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint64_t *out,
+                          cudaStream_t s) {
+    const bool cubic = h.gamma == MPHF_GAMMA_CUBIC, pow2 = h.reduce == kReducePow2;
+    const bool vec = h.remap == MPHF_REMAP_VEC;
+#define MPHF_WIDE_CASE(G, R)                                                         \
+    return vec ? launch_u64_wide_t<G, R, kRemapVec>(v, keys, count, out, s)      \
+               : launch_u64_wide_t<G, R, kRemapClef>(v, keys, count, out, s);
+    if (cubic && pow2) { MPHF_WIDE_CASE(MPHF_GAMMA_CUBIC, kReducePow2) }
+    if (cubic) { MPHF_WIDE_CASE(MPHF_GAMMA_CUBIC, kReduceMod) }
+    if (pow2) { MPHF_WIDE_CASE(MPHF_GAMMA_LINEAR, kReducePow2) }
+    MPHF_WIDE_CASE(MPHF_GAMMA_LINEAR, kReduceMod)
+#undef MPHF_WIDE_CASE
+}
+
 int launch_query_u64(const Header &h, const View &v, const uint64_t *keys, uint64_t count,
                      uint32_t *out, bool phf, cudaStream_t s) {
     const bool cubic = h.gamma == MPHF_GAMMA_CUBIC;
@@ -125,10 +190,10 @@ constexpr int kBlkStage = kStrThreads * 64 + 64;     // staged bytes per block
 // whole key buffer may be read; only the chunk crossing that end is read
 // byte by byte), then each thread hashes its string from the stage.  A
 // block whose bytes do not fit the stage hashes from global memory.
-template <int GAMMA, int REDUCE, int REMAP>
+template <int GAMMA, int REDUCE, int REMAP, bool WIDE>
 __global__ void __launch_bounds__(kStrThreads)
 query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
-                   const uint64_t count, uint32_t *__restrict__ out) {
+                   const uint64_t count, void *__restrict__ out) {
     __shared__ __align__(16) uint8_t stage[kBlkStage];
     const int t = threadIdx.x;
     const uint64_t i0 = (uint64_t)blockIdx.x * kStrThreads;
@@ -167,36 +232,48 @@ query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64
     uint64_t part;
     const uint64_t b = bucket_of<GAMMA>(v, h, part);
     const uint32_t p = __ldg(v.pilots + b);
-    out[i] = slot_value<REDUCE, REMAP, false>(v, h, part, p);
+    if constexpr (WIDE) static_cast<uint64_t *>(out)[i] = slot_value_wide<REDUCE, REMAP>(v, h, part, p);
+    else static_cast<uint32_t *>(out)[i] = slot_value<REDUCE, REMAP, false>(v, h, part, p);
 }
 
-template <int GAMMA, int REDUCE, int REMAP>
+template <int GAMMA, int REDUCE, int REMAP, bool WIDE>
 static int launch_bytes_t(const View &v, const uint8_t *bytes, const uint64_t *offsets, uint64_t count,
-                          uint32_t *out, cudaStream_t s) {
+                          void *out, cudaStream_t s) {
     const uint64_t blocks = (count + kStrThreads - 1) / kStrThreads;
     if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
     if ((uintptr_t)bytes % 16) {
         set_error("byte keys need a 16-byte aligned buffer");
         return MPHF_ERR_ARG;
     }
-    query_bytes_kernel<GAMMA, REDUCE, REMAP><<<(unsigned)blocks, kStrThreads, 0, s>>>(v, bytes, offsets, count, out);
+    query_bytes_kernel<GAMMA, REDUCE, REMAP, WIDE><<<(unsigned)blocks, kStrThreads, 0, s>>>(v, bytes, offsets, count, out);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "query_bytes launch");
 }
 
-int launch_query_bytes(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
-                       uint64_t count, uint32_t *out, cudaStream_t s) {
+template <bool WIDE>
+static int dispatch_bytes(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
+                          uint64_t count, void *out, cudaStream_t s) {
     const bool cubic = h.gamma == MPHF_GAMMA_CUBIC, pow2 = h.reduce == kReducePow2;
     const bool vec = h.remap == MPHF_REMAP_VEC;
-#define MPHF_BYTES_CASE(G, R)                                                            \
-    return vec ? launch_bytes_t<G, R, kRemapVec>(v, bytes, offsets, count, out, s)     \
-               : launch_bytes_t<G, R, kRemapClef>(v, bytes, offsets, count, out, s);
+#define MPHF_BYTES_CASE(G, R)                                                                  \
+    return vec ? launch_bytes_t<G, R, kRemapVec, WIDE>(v, bytes, offsets, count, out, s)     \
+               : launch_bytes_t<G, R, kRemapClef, WIDE>(v, bytes, offsets, count, out, s);
     if (cubic && pow2) { MPHF_BYTES_CASE(MPHF_GAMMA_CUBIC, kReducePow2) }
     if (cubic) { MPHF_BYTES_CASE(MPHF_GAMMA_CUBIC, kReduceMod) }
     if (pow2) { MPHF_BYTES_CASE(MPHF_GAMMA_LINEAR, kReducePow2) }
     MPHF_BYTES_CASE(MPHF_GAMMA_LINEAR, kReduceMod)
 #undef MPHF_BYTES_CASE
+}
+
+int launch_query_bytes(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
+                       uint64_t count, uint32_t *out, cudaStream_t s) {
+    return dispatch_bytes<false>(h, v, bytes, offsets, count, out, s);
+}
+
+int launch_query_bytes_wide(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
+                            uint64_t count, uint64_t *out, cudaStream_t s) {
+    return dispatch_bytes<true>(h, v, bytes, offsets, count, out, s);
 }
 
 // Key hashes for the builder: h = C k for u64 keys, the string hash above

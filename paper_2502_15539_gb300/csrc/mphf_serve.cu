@@ -41,7 +41,7 @@
 using Clock = std::chrono::steady_clock;
 
 namespace ptrhash {
-int serialized_device_bytes(const void *blob, size_t len, uint64_t *bytes);
+int serialized_device_bytes(const void *blob, size_t len, uint64_t *bytes, uint64_t *n);
 int handle_in_arena(const void *blob, size_t len, uint8_t *dev, cudaStream_t s, mphf_t **out);
 }  // namespace ptrhash
 
@@ -405,8 +405,10 @@ void mphf_server_free(mphf_server_t *s) {
 int mphf_server_add(mphf_server_t *s, const void *serialized, size_t len, uint32_t *id) {
     if (!s || !serialized || !id) { ptrhash::set_error("NULL argument"); return MPHF_ERR_ARG; }
     Entry e;
-    int rc = ptrhash::serialized_device_bytes(serialized, len, &e.dev_bytes);
+    uint64_t n = 0;
+    int rc = ptrhash::serialized_device_bytes(serialized, len, &e.dev_bytes, &n);
     if (rc) return rc;
+    if (ptrhash::wide_values(n)) { ptrhash::set_error("n > 2^32: the server returns 32-bit results"); return MPHF_ERR_ARG; }
     if (e.dev_bytes > s->arena.cap) {
         ptrhash::set_error("structure of %llu bytes exceeds the HBM budget", (unsigned long long)e.dev_bytes);
         return MPHF_ERR_CAPACITY;

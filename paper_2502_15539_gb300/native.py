@@ -144,6 +144,8 @@ SIGNATURES = {
     "mphf_server_stats": (_i32, [_vp, ctypes.c_int, ctypes.POINTER(mphf_server_stats_t)]),
     "mphf_server_free": (None, [_vp]),
     "mphf_device_view": (_i32, [_vp, ctypes.POINTER(mphf_view_t)]),
+    "mphf_query_u64_wide": (_i32, [_vp, _vp, _u64, _vp, _vp]),
+    "mphf_query_bytes_wide": (_i32, [_vp, _vp, _vp, _u64, _vp, _vp]),
 }
 
 _lock = threading.Lock()
@@ -244,6 +246,28 @@ def mphf_build(keys: torch.Tensor, params: mphf_params | None = None, offsets: t
     _check(load().mphf_build(ctypes.byref(params), kind, kp, op, n, _stream(stream), ctypes.byref(out)),
            "mphf_build")
     return MPHF(out.value)
+
+
+def mphf_query_u64_wide(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """64-bit results (int64 tensor holding the u64 values); any structure."""
+    if out is None:
+        out = torch.empty(keys.numel(), dtype=torch.int64, device=keys.device)
+    if not _u64_dtype_ok(keys):
+        raise ValueError("keys must be int64")
+    _check(load().mphf_query_u64_wide(m.handle, _dev_ptr(keys, keys.dtype, "keys"), keys.numel(),
+                                      _dev_ptr(out, torch.int64, "out"), _stream(stream)), "mphf_query_u64_wide")
+    return out
+
+
+def mphf_query_bytes_wide(m: MPHF, data: torch.Tensor, offsets: torch.Tensor, out: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    count = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(count, dtype=torch.int64, device=data.device)
+    _check(load().mphf_query_bytes_wide(m.handle, _dev_ptr(data, torch.uint8, "bytes"),
+                                        _dev_ptr(offsets, torch.int64, "offsets"), count,
+                                        _dev_ptr(out, torch.int64, "out"), _stream(stream)), "mphf_query_bytes_wide")
+    return out
 
 
 def mphf_query_u64(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

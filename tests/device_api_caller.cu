@@ -33,6 +33,11 @@ __global__ void count_u64_kernel(mphf_view_t v, const uint64_t *keys, uint64_t n
         atomicAdd(counts + mphf_dev::eval_u64(v, keys[i]), 1u);
 }
 
+__global__ void eval_u64_wide_kernel(mphf_view_t v, const uint64_t *keys, uint64_t n, uint64_t *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = mphf_dev::eval_u64_wide(v, keys[i]);
+}
+
 __global__ void slot_u64_kernel(mphf_view_t v, const uint64_t *keys, uint64_t n, uint64_t *out) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         out[i] = mphf_dev::slot_hash(v, v.C * keys[i]);
@@ -55,6 +60,11 @@ int caller_eval_bytes(const mphf_view_t *v, const uint8_t *bytes, const uint64_t
 
 int caller_count_u64(const mphf_view_t *v, const uint64_t *keys, uint64_t n, uint32_t *counts, void *stream) {
     if (n) count_u64_kernel<<<grid_for(n), kThreads, 0, (cudaStream_t)stream>>>(*v, keys, n, counts);
+    return (int)cudaGetLastError();
+}
+
+int caller_eval_u64_wide(const mphf_view_t *v, const uint64_t *keys, uint64_t n, uint64_t *out, void *stream) {
+    if (n) eval_u64_wide_kernel<<<grid_for(n), kThreads, 0, (cudaStream_t)stream>>>(*v, keys, n, out);
     return (int)cudaGetLastError();
 }
 

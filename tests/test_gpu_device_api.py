@@ -37,7 +37,7 @@ def ids(c):
 def caller():
     lib = ctypes.CDLL(caller_library())
     vp = ctypes.c_void_p
-    for name in ("caller_eval_u64", "caller_count_u64", "caller_slot_u64"):
+    for name in ("caller_eval_u64", "caller_count_u64", "caller_slot_u64", "caller_eval_u64_wide"):
         getattr(lib, name).argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
         getattr(lib, name).restype = ctypes.c_int
     lib.caller_eval_bytes.argtypes = [vp, vp, vp, ctypes.c_uint64, vp, vp]
@@ -66,6 +66,10 @@ def test_caller_kernel_matches_oracle(case):
     got = u32(out)
     assert np.array_equal(got, want), f"{int((got != want).sum())} mismatches"
     assert np.array_equal(got, u32(N.mphf_query_u64(m, q)))
+
+    wide = torch.empty(q.numel(), dtype=torch.int64, device="cuda")
+    assert lib.caller_eval_u64_wide(ctypes.byref(view), q.data_ptr(), q.numel(), wide.data_ptr(), stream()) == 0
+    assert np.array_equal(wide.cpu().numpy().view(np.uint64), want)
 
     slots = torch.empty(q.numel(), dtype=torch.int64, device="cuda")
     assert lib.caller_slot_u64(ctypes.byref(view), q.data_ptr(), q.numel(), slots.data_ptr(), stream()) == 0

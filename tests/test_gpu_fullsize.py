@@ -27,10 +27,12 @@ def sample_positions(n: int, m: int = 1_000_000, seed: int = 5) -> torch.Tensor:
 
 
 def assert_bijection_on_device(out: torch.Tensor, n: int):
+    vals = out.to(torch.int64) & 0xFFFFFFFF
+    assert int(vals.max().item()) < n   # checked first: the fill below must stay in bounds
     seen = torch.zeros(n, dtype=torch.int32, device=out.device)
-    seen.index_fill_(0, out.to(torch.int64) & 0xFFFFFFFF, 1)
+    seen.index_fill_(0, vals, 1)
     assert int(seen.sum().item()) == n
-    del seen
+    del seen, vals
 
 
 def test_u64_1e9_keys():
@@ -105,3 +107,36 @@ def test_batch_256_structures():
     torch.cuda.synchronize()
     for ref, q, (_, _, out) in zip(refs, queries, items):
         assert np.array_equal(u32(out), ref.query_u64(W.as_uint64_numpy(q), threads=CORES))
+
+
+def test_u64_past_2_32_keys():
+    """n = 4.5e9 > 2^32 distinct u64 keys: the GPU build (in shards of whole
+    parts, Appendix B) and the 64-bit-result query over every key.  The
+    result is a bijection onto [0, n) (a device bitmap), and a seeded sample
+    of keys, plus keys whose values pass 2^32, agree with the oracle's
+    evaluation of the serialized structure."""
+    N = need_gpu()
+    n = 4_500_000_000
+    chunk = 1 << 28
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    for s in range(0, n, chunk):
+        keys[s:s + chunk] = W.u64_keys(min(chunk, n - s), seed=3, device="cuda", start=s)
+    m = N.mphf_build(keys)
+    info = N.mphf_info(m)
+    assert info["n"] == n and info["P"] * info["S"] > (1 << 32)
+    out = N.mphf_query_u64_wide(m, keys)
+    torch.cuda.synchronize()
+    assert int(out.min().item()) >= 0 and int(out.max().item()) < n   # the fill below stays in bounds
+    seen = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    seen.index_fill_(0, out, 1)
+    assert int(seen.sum(dtype=torch.int64).item()) == n
+    del seen
+    idx = torch.cat([W.uniform_index(1_000_000, n, 11, device="cuda"),
+                     torch.nonzero(out > (1 << 32))[:1000, 0]])
+    got = out[idx].cpu().numpy().view(np.uint64)
+    sample = keys[idx].cpu()
+    del keys, out
+    torch.cuda.empty_cache()
+    ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
+    assert ref.wide
+    assert np.array_equal(got, ref.query_u64(W.as_uint64_numpy(sample), threads=CORES))

@@ -55,6 +55,30 @@ def test_query_u64_matches_oracle(case):
     assert got.max() < n
 
 
+@pytest.mark.parametrize("case", CASES[2:10], ids=[ids(c) for c in CASES[2:10]])
+def test_wide_query_matches_oracle(case):
+    """The 64-bit-result query (needed past 2^32 keys) gives the same values."""
+    N = need_gpu()
+    n, params = case
+    ref, blob = oracle_structure(n, 0, **params)
+    m = N.mphf_deserialize(blob)
+    q = torch.cat([W.u64_keys(n, 0)[W.permutation(n, 1)], W.nonmember_u64_keys(max(n // 4, 17), n, 0)])
+    got = N.mphf_query_u64_wide(m, q.cuda()).cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, ref.query_u64(W.as_uint64_numpy(q)))
+
+
+@pytest.mark.parametrize("n,params", [(5000, {}), (100_000, {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC})])
+def test_wide_bytes_query_matches_oracle(n, params):
+    N = need_gpu()
+    ids_ = torch.arange(n)
+    data, off = W.strings(ids_, seed=3)
+    ref = O.OracleMPHF.build_bytes(data.numpy(), off.numpy().astype(np.uint64), threads=8, **params)
+    m = N.mphf_deserialize(ref.serialize())
+    qd, qo = W.strings(torch.cat([ids_[W.permutation(n, 1)], torch.arange(n, n + n // 4)]), seed=3)
+    got = N.mphf_query_bytes_wide(m, qd.cuda(), qo.cuda()).cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, ref.query_bytes(qd.numpy(), qo.numpy().astype(np.uint64)))
+
+
 @pytest.mark.parametrize("case", CASES[4:9], ids=[ids(c) for c in CASES[4:9]])
 def test_phf_query_matches_oracle_slots(case):
     N = need_gpu()
