@@ -72,6 +72,11 @@ typedef struct {
                                  Appendix B); 0: automatic, from the free
                                  device memory.  The structure is the same
                                  for every value.                             */
+    int32_t  hash128;         /* byte keys: 1 = the 128-bit string hash (the
+                                 high half picks part and bucket, the low half
+                                 the slot, Sec. 3.1); 0 = only when n > 2^32.
+                                 u64 keys ignore it (h = C k is injective).   */
+    int32_t  reserved;        /* 0                                            */
 } mphf_params;
 
 /* Fills *p with the Default parameters.  Returns MPHF_ERR_ARG for NULL. */
@@ -361,6 +366,9 @@ typedef struct {
                                   1: reduce(x) = x mod S (Sec. 3.1)              */
     int32_t  remap_kind;       /* MPHF_REMAP_*                                   */
     int32_t  key_kind;         /* MPHF_KEY_*                                     */
+    int32_t  hash128;          /* byte keys: 1 = 128-bit string hash (its high
+                                  half picks part and bucket, Sec. 3.1)          */
+    int32_t  reserved;
 } mphf_view_t;
 
 /* Fills *out with the structure's device view, for fusing the evaluation

@@ -123,22 +123,33 @@ __device__ __forceinline__ uint64_t str_finish(uint64_t acc, uint64_t len, uint6
     return str_mix(acc ^ (len * kStrK2) ^ seed);
 }
 
+// 128-bit variant (beyond 2^32 keys, Sec. 3.1): the low half is the hash
+// above, the high half the same construction with seed xor K4 and the fold
+// constant K5; the high half picks the part and bucket, the low half the slot.
+constexpr uint64_t kStrK4 = 0x47523634D9D6709Bull;
+constexpr uint64_t kStrK5 = 0x2EF8175451B07575ull;
+__device__ __forceinline__ uint64_t str_fold_hi(uint64_t x) { return mul_hi(x, kStrK5) ^ (x * kStrK5); }
+
 // The string hash over 32-bit little-endian words W[0], W[1], ... that hold
 // the string from bit `sh` (0, 8, 16 or 24) of W[0] on.  Word j of the
 // string is bits [64 j + sh, 64 j + sh + 64) of that sequence: two funnel
 // shifts of W[2j], W[2j+1], W[2j+2].  fetch(k) returns W[k]; it is called
-// for every k <= 2 ceil(len / 8).
-// Len is the integer type of the length and word indexes (32 bits where
-// the string is known to be short).
-template <class Fetch, class Len>
-__device__ __forceinline__ uint64_t hash_string_words(Fetch fetch, uint32_t sh, Len len, uint64_t seed) {
-    uint64_t acc = 0, tweak = seed;
+// for every k <= 2 ceil(len / 8).  out[0] gets the 64-bit hash and, with
+// H128, out[1] the high half of the 128-bit one.  Len is the integer type
+// of the length and word indexes (32 bits where the string is known to be
+// short).
+template <bool H128, class Fetch, class Len>
+__device__ __forceinline__ void hash_string_words_n(Fetch fetch, uint32_t sh, Len len, uint64_t seed,
+                                                    uint64_t *out) {
+    const uint64_t seed_hi = seed ^ kStrK4;
+    uint64_t acc = 0, acc_hi = 0, tweak = seed, tweak_hi = seed_hi;
     uint32_t cur = fetch(Len(0));
     const Len full = len >> 3;
-    for (Len j = 0; j < full; j++, tweak += kStrK1) {
+    for (Len j = 0; j < full; j++, tweak += kStrK1, tweak_hi += kStrK1) {
         const uint32_t m1 = fetch(2 * j + 1), m2 = fetch(2 * j + 2);
         const uint64_t w = ((uint64_t)__funnelshift_r(m1, m2, sh) << 32) | __funnelshift_r(cur, m1, sh);
         acc += str_fold(w ^ tweak);
+        if (H128) acc_hi += str_fold_hi(w ^ tweak_hi);
         cur = m2;
     }
     const uint32_t rem = (uint32_t)len & 7u;
@@ -147,49 +158,75 @@ __device__ __forceinline__ uint64_t hash_string_words(Fetch fetch, uint32_t sh, 
         uint64_t w = ((uint64_t)__funnelshift_r(m1, m2, sh) << 32) | __funnelshift_r(cur, m1, sh);
         w &= (1ull << (8 * rem)) - 1;
         acc += str_fold(w ^ tweak);
+        if (H128) acc_hi += str_fold_hi(w ^ tweak_hi);
     }
-    return str_finish(acc, (uint64_t)len, seed);
+    out[0] = str_finish(acc, (uint64_t)len, seed);
+    if (H128) out[1] = str_finish(acc_hi, (uint64_t)len, seed_hi);
+}
+
+template <class Fetch, class Len>
+__device__ __forceinline__ uint64_t hash_string_words(Fetch fetch, uint32_t sh, Len len, uint64_t seed) {
+    uint64_t h[1];
+    hash_string_words_n<false>(fetch, sh, len, seed, h);
+    return h[0];
 }
 
 // The string hash of bytes[a, a + len) in global memory, read as aligned
 // 32-bit words; words that hold no byte of the string are not read.
-__device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uint64_t a, uint64_t len,
-                                                       uint64_t seed) {
+// out[0] = the 64-bit hash; with H128 out[1] = the high half.
+template <bool H128>
+__device__ __forceinline__ void hash_string_global_n(const uint8_t *bytes, uint64_t a, uint64_t len, uint64_t seed,
+                                                     uint64_t *out) {
     const uintptr_t addr = reinterpret_cast<uintptr_t>(bytes + a);
     const uint32_t *w = reinterpret_cast<const uint32_t *>(addr & ~(uintptr_t)3);
     const uint64_t lead = addr & 3;   // bytes of W[0] before the string
-    return hash_string_words([&](uint64_t k) { return 4 * k < lead + len ? __ldg(w + k) : 0u; },
-                             (uint32_t)(8 * lead), len, seed);
+    hash_string_words_n<H128>([&](uint64_t k) { return 4 * k < lead + len ? __ldg(w + k) : 0u; },
+                              (uint32_t)(8 * lead), len, seed, out);
 }
 
-// The non-minimal slot of a key hash (Eq. slot): part S + reduce(h xor hp(p), S).
-__device__ __forceinline__ uint64_t slot_hash(const mphf_view_t &v, uint64_t h) {
-    const uint64_t part = mul_hi(v.P, h);
-    const uint64_t x = v.P * h;   // position inside the part, as a fraction of 2^64
+__device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uint64_t a, uint64_t len,
+                                                       uint64_t seed) {
+    uint64_t h[1];
+    hash_string_global_n<false>(bytes, a, len, seed, h);
+    return h[0];
+}
+
+// The non-minimal slot (Eq. slot): part S + reduce(hs xor hp(p), S), with
+// the part and bucket taken from hb (Eq. partbucket).  hb = hs except for
+// 128-bit string hashes.
+__device__ __forceinline__ uint64_t slot_hash2(const mphf_view_t &v, uint64_t hb, uint64_t hs) {
+    const uint64_t part = mul_hi(v.P, hb);
+    const uint64_t x = v.P * hb;   // position inside the part, as a fraction of 2^64
     const uint64_t g = v.gamma == MPHF_GAMMA_CUBIC ? bucket_fn<MPHF_GAMMA_CUBIC>(x) : x;
     const uint64_t b = part * v.B + mul_hi(v.B, g);
-    const uint64_t xp = h ^ (v.C * ((uint64_t)__ldg(v.pilots + b) ^ v.seed));
+    const uint64_t xp = hs ^ (v.C * ((uint64_t)__ldg(v.pilots + b) ^ v.seed));
     const uint64_t r = v.reduce == 0 ? (mul_hi(v.C, xp) & v.s_mask) : mod_barrett(xp, v.barrett, v.S);
     return part * v.S + r;
 }
 
-// The MPHF value of a key hash: the slot, or its remap entry when >= n.
+__device__ __forceinline__ uint64_t slot_hash(const mphf_view_t &v, uint64_t h) { return slot_hash2(v, h, h); }
+
+// The MPHF value of a slot: itself, or its remap entry when >= n.
 // The 32-bit forms need n <= 2^32; the _wide forms take any structure.
-__device__ __forceinline__ uint32_t eval_hash(const mphf_view_t &v, uint64_t h) {
-    const uint64_t s = slot_hash(v, h);
+__device__ __forceinline__ uint32_t eval_slot(const mphf_view_t &v, uint64_t s) {
     if (s < v.n) return (uint32_t)s;
     const uint32_t j = (uint32_t)(s - v.n);
     if (v.remap_kind == MPHF_REMAP_CLEF) return clef_get(static_cast<const uint8_t *>(v.remap), j);
     return __ldg(static_cast<const uint32_t *>(v.remap) + j);
 }
 
-__device__ __forceinline__ uint64_t eval_hash_wide(const mphf_view_t &v, uint64_t h) {
-    const uint64_t s = slot_hash(v, h);
+__device__ __forceinline__ uint64_t eval_slot_wide(const mphf_view_t &v, uint64_t s) {
     if (s < v.n) return s;
     const uint64_t j = s - v.n;
     if (v.remap_kind == MPHF_REMAP_CLEF) return clef_get64(static_cast<const uint8_t *>(v.remap), j);
     if (v.n > (1ull << 32)) return __ldg(static_cast<const unsigned long long *>(v.remap) + j);
     return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+}
+
+// The value of a key hash (u64 keys, and strings with the 64-bit hash).
+__device__ __forceinline__ uint32_t eval_hash(const mphf_view_t &v, uint64_t h) { return eval_slot(v, slot_hash(v, h)); }
+__device__ __forceinline__ uint64_t eval_hash_wide(const mphf_view_t &v, uint64_t h) {
+    return eval_slot_wide(v, slot_hash(v, h));
 }
 
 // A u64 key (structures built with MPHF_KEY_U64).
@@ -199,12 +236,22 @@ __device__ __forceinline__ uint64_t eval_u64_wide(const mphf_view_t &v, uint64_t
     return eval_hash_wide(v, v.C * key);
 }
 
-// A byte-string key (structures built with MPHF_KEY_BYTES).
+// A byte-string key (structures built with MPHF_KEY_BYTES), with the
+// structure's 64- or 128-bit string hash.
+__device__ __forceinline__ uint64_t slot_bytes(const mphf_view_t &v, const uint8_t *s, uint64_t len) {
+    uint64_t h[2];
+    if (v.hash128) {
+        hash_string_global_n<true>(s, 0, len, v.seed, h);
+        return slot_hash2(v, h[1], h[0]);
+    }
+    hash_string_global_n<false>(s, 0, len, v.seed, h);
+    return slot_hash(v, h[0]);
+}
 __device__ __forceinline__ uint32_t eval_bytes(const mphf_view_t &v, const uint8_t *s, uint64_t len) {
-    return eval_hash(v, hash_string_global(s, 0, len, v.seed));
+    return eval_slot(v, slot_bytes(v, s, len));
 }
 __device__ __forceinline__ uint64_t eval_bytes_wide(const mphf_view_t &v, const uint8_t *s, uint64_t len) {
-    return eval_hash_wide(v, hash_string_global(s, 0, len, v.seed));
+    return eval_slot_wide(v, slot_bytes(v, s, len));
 }
 
 }  // namespace mphf_dev

@@ -63,7 +63,7 @@ class Params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("C", ctypes.c_uint64),
                 ("slots_override", ctypes.c_uint64), ("max_reseeds", ctypes.c_int32),
                 ("evict_mult", ctypes.c_uint32), ("threads", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("hash128", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -95,6 +95,9 @@ def lib():
             L.orc_gamma.restype = u64; L.orc_gamma.argtypes = [i32, u64]
             L.orc_hash_u64.restype = u64; L.orc_hash_u64.argtypes = [u64, u64]
             L.orc_hash_bytes.restype = u64; L.orc_hash_bytes.argtypes = [vp, u64, u64]
+            L.orc_hash_bytes128.restype = None
+            L.orc_hash_bytes128.argtypes = [vp, u64, u64, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+            L.orc_slot_of_hash2.restype = u64; L.orc_slot_of_hash2.argtypes = [vp, u64, u64]
             L.orc_hp.restype = u64; L.orc_hp.argtypes = [u64, u64, u64]
             L.orc_reduce.restype = u64; L.orc_reduce.argtypes = [i32, u64, u64, u64]
             L.orc_part_bucket.restype = None
@@ -157,6 +160,14 @@ def gamma(kind: int, x: int) -> int:
 def hash_bytes(data: bytes, seed: int) -> int:
     buf = np.frombuffer(data, dtype=np.uint8) if data else np.zeros(1, np.uint8)
     return lib().orc_hash_bytes(_ptr(buf), len(data), seed)
+
+
+def hash_bytes128(data: bytes, seed: int) -> tuple[int, int]:
+    """(hi, lo) of the 128-bit string hash; lo == hash_bytes(data, seed)."""
+    buf = np.frombuffer(data, dtype=np.uint8) if data else np.zeros(1, np.uint8)
+    hi, lo = ctypes.c_uint64(), ctypes.c_uint64()
+    lib().orc_hash_bytes128(_ptr(buf), len(data), seed, ctypes.byref(hi), ctypes.byref(lo))
+    return hi.value, lo.value
 
 
 def reduce(kind: int, C: int, x: int, S: int) -> int:

@@ -80,10 +80,10 @@ void orc_part_bucket(const orc_layout *L, int gamma, uint64_t h,
  *   mix(z)  = splitmix64 finalizer (Steele, Lea, Flood 2014):
  *             z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27;
  *             z *= 0x94D049BB133111EB; z ^= z>>31
- * with K1 = 0x9E3779B97F4A7C15, K2 = 0xC2B2AE3D27D4EB4F and
- * K3 = 0xA173621FA8385BE3.  The sum makes the words independent of each
- * other, so any split of the words over parallel workers gives the same
- * value; one multiply per word keeps the per-word work small. */
+ * with K1 = 0x9E3779B97F4A7C15, K2 = 0xC2B2AE3D27D4EB4F and the fold
+ * constant K3 = 0xA173621FA8385BE3.  The sum makes the words independent of
+ * each other, so any split of the words over parallel workers gives the
+ * same value; one multiply per word keeps the per-word work small. */
 static uint64_t str_mix(uint64_t z) {
     z ^= z >> 30;
     z *= 0xBF58476D1CE4E5B9ull;
@@ -93,12 +93,12 @@ static uint64_t str_mix(uint64_t z) {
     return z;
 }
 
-static uint64_t str_fold(uint64_t x) {
-    const unsigned __int128 p = (unsigned __int128)x * 0xA173621FA8385BE3ull;
+static uint64_t str_fold(uint64_t x, uint64_t K3) {
+    const unsigned __int128 p = (unsigned __int128)x * K3;
     return (uint64_t)(p >> 64) ^ (uint64_t)p;
 }
 
-uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed) {
+static uint64_t hash_words(const uint8_t *s, uint64_t len, uint64_t seed, uint64_t K3) {
     const uint64_t K1 = 0x9E3779B97F4A7C15ull, K2 = 0xC2B2AE3D27D4EB4Full;
     uint64_t acc = 0;
     uint64_t nwords = (len + 7) / 8;
@@ -109,9 +109,22 @@ uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed) {
             uint64_t byte = pos < len ? s[pos] : 0;
             w |= byte << (8 * b);
         }
-        acc += str_fold(w ^ (seed + j * K1));
+        acc += str_fold(w ^ (seed + j * K1), K3);
     }
     return str_mix(acc ^ (len * K2) ^ seed);
+}
+
+uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed) {
+    return hash_words(s, len, seed, 0xA173621FA8385BE3ull);
+}
+
+/* 128-bit variant (Sec. 3.1: beyond 2^32 keys, a 128-bit string hash whose
+ * high half picks the part and bucket and whose low half the slot):
+ * lo = the 64-bit hash; hi = the same construction with seed xor K4 and the
+ * fold constant K5, K4 = 0x47523634D9D6709B, K5 = 0x2EF8175451B07575. */
+void orc_hash_bytes128(const uint8_t *s, uint64_t len, uint64_t seed, uint64_t *hi, uint64_t *lo) {
+    *lo = orc_hash_bytes(s, len, seed);
+    *hi = hash_words(s, len, seed ^ 0x47523634D9D6709Bull, 0x2EF8175451B07575ull);
 }
 
 /* ------------------------------------------------------------------ */
@@ -249,11 +262,15 @@ uint64_t orc_clef_get(const uint8_t *lines, uint64_t j) {
 /* ------------------------------------------------------------------ */
 
 /* slot(k) = part * S + reduce(h xor hp(p_bucket), S)   (Eq. slot) */
-uint64_t orc_slot_of_hash(const orc_mphf *m, uint64_t h) {
+uint64_t orc_slot_of_hash(const orc_mphf *m, uint64_t h) { return orc_slot_of_hash2(m, h, h); }
+
+/* 128-bit string hashes: hb (the high half) picks the part and bucket in
+ * Eq. partbucket, hs (the low half) enters Eq. slot. */
+uint64_t orc_slot_of_hash2(const orc_mphf *m, uint64_t hb, uint64_t hs) {
     uint64_t part, b;
-    orc_part_bucket(&m->L, m->gamma, h, &part, &b);
+    orc_part_bucket(&m->L, m->gamma, hb, &part, &b);
     uint64_t pilot = m->pilots[part * m->L.B + b];
-    uint64_t x = h ^ orc_hp(m->C, m->seed, pilot);
+    uint64_t x = hs ^ orc_hp(m->C, m->seed, pilot);
     return part * m->L.S + orc_reduce(m->L.reduce, m->C, x, m->L.S);
 }
 
@@ -265,6 +282,12 @@ static uint64_t remap_get(const orc_mphf *m, uint64_t j) {
 /* A slot >= n is replaced by F[slot - n] (Sec. 3.4, "Remapping"). */
 uint64_t orc_query_hash(const orc_mphf *m, uint64_t h) {
     uint64_t s = orc_slot_of_hash(m, h);
+    if (s < m->L.n) return s;
+    return remap_get(m, s - m->L.n);
+}
+
+static uint64_t query_hash2(const orc_mphf *m, uint64_t hb, uint64_t hs) {
+    uint64_t s = orc_slot_of_hash2(m, hb, hs);
     if (s < m->L.n) return s;
     return remap_get(m, s - m->L.n);
 }
@@ -289,7 +312,13 @@ static void *query_bytes_worker(void *arg) {
     query_job *J = (query_job *)arg;
     for (uint64_t i = J->lo; i < J->hi; i++) {
         uint64_t a = J->offsets[i], b = J->offsets[i + 1];
-        J->out[i] = orc_query_hash(J->m, orc_hash_bytes(J->bytes + a, b - a, J->m->seed));
+        if (J->m->hash128) {
+            uint64_t hi, lo;
+            orc_hash_bytes128(J->bytes + a, b - a, J->m->seed, &hi, &lo);
+            J->out[i] = query_hash2(J->m, hi, lo);
+        } else {
+            J->out[i] = orc_query_hash(J->m, orc_hash_bytes(J->bytes + a, b - a, J->m->seed));
+        }
     }
     return NULL;
 }
@@ -339,9 +368,19 @@ static int cmp_u64(const void *a, const void *b) {
     return x < y ? -1 : x > y;
 }
 
+typedef struct { uint64_t hi, lo; } pair128;
+
+static int cmp_pair128(const void *a, const void *b) {
+    const pair128 *x = (const pair128 *)a, *y = (const pair128 *)b;
+    if (x->hi != y->hi) return x->hi < y->hi ? -1 : 1;
+    return x->lo < y->lo ? -1 : x->lo > y->lo;
+}
+
 /* Per-part state of the pilot search. */
 typedef struct {
-    uint64_t *h;          /* the part's hashes, sorted                     */
+    uint64_t *h;          /* the part's slot hashes, sorted                */
+    uint64_t *hb;         /* its bucket hashes: h itself, or the high halves
+                             of 128-bit hashes (sorted by (hb, h))         */
     uint64_t cnt;
     uint32_t *start;      /* B+1 bucket offsets into h                     */
     uint32_t *owner;      /* S entries: bucket that holds the slot, or NONE */
@@ -423,15 +462,26 @@ static int build_part(const build_ctx *bc, part_state *ps, uint64_t part,
     *evictions_out = 0;
 
     /* Sort the part's hashes; equal neighbours are duplicate keys. */
-    qsort(ps->h, ps->cnt, sizeof(uint64_t), cmp_u64);
-    for (uint64_t i = 1; i < ps->cnt; i++)
-        if (ps->h[i] == ps->h[i - 1]) return ORC_ERR_DUP_KEYS;
+    if (ps->hb == ps->h) {
+        qsort(ps->h, ps->cnt, sizeof(uint64_t), cmp_u64);
+        for (uint64_t i = 1; i < ps->cnt; i++)
+            if (ps->h[i] == ps->h[i - 1]) return ORC_ERR_DUP_KEYS;
+    } else {   /* 128-bit hashes: sort the pairs (hb, h) */
+        pair128 *pr = (pair128 *)malloc((ps->cnt + 1) * sizeof(pair128));
+        if (!pr) return ORC_ERR_OOM;
+        for (uint64_t i = 0; i < ps->cnt; i++) { pr[i].hi = ps->hb[i]; pr[i].lo = ps->h[i]; }
+        qsort(pr, ps->cnt, sizeof(pair128), cmp_pair128);
+        for (uint64_t i = 0; i < ps->cnt; i++) { ps->hb[i] = pr[i].hi; ps->h[i] = pr[i].lo; }
+        free(pr);
+        for (uint64_t i = 1; i < ps->cnt; i++)
+            if (ps->hb[i] == ps->hb[i - 1] && ps->h[i] == ps->h[i - 1]) return ORC_ERR_DUP_KEYS;
+    }
 
     /* Bucket boundaries by counting (sorted hashes fall in bucket order). */
     for (uint64_t b = 0; b <= B; b++) ps->start[b] = 0;
     for (uint64_t i = 0; i < ps->cnt; i++) {
         uint64_t pp, b;
-        orc_part_bucket(&m->L, m->gamma, ps->h[i], &pp, &b);
+        orc_part_bucket(&m->L, m->gamma, ps->hb[i], &pp, &b);
         ps->start[b + 1]++;
     }
     for (uint64_t b = 0; b < B; b++) ps->start[b + 1] += ps->start[b];
@@ -533,6 +583,7 @@ static int build_part(const build_ctx *bc, part_state *ps, uint64_t part,
 typedef struct {
     const build_ctx *bc;
     const uint64_t *by_part;    /* hashes grouped by part                   */
+    const uint64_t *by_part_hi; /* their high halves (128-bit), else NULL   */
     const uint64_t *part_start; /* P+1 offsets                              */
     uint8_t *taken;
     uint64_t next_part;         /* shared work counter                      */
@@ -552,10 +603,11 @@ static void *build_worker(void *arg) {
         if (c > max_cnt) max_cnt = c;
     }
     ps.h = (uint64_t *)malloc((max_cnt + 1) * sizeof(uint64_t));
+    ps.hb = bp->by_part_hi ? (uint64_t *)malloc((max_cnt + 1) * sizeof(uint64_t)) : ps.h;
     ps.start = (uint32_t *)malloc((m->L.B + 1) * sizeof(uint32_t));
     ps.owner = (uint32_t *)malloc(m->L.S * sizeof(uint32_t));
     ps.heap = (uint32_t *)malloc(m->L.B * sizeof(uint32_t));
-    int rc = (ps.h && ps.start && ps.owner && ps.heap) ? ORC_OK : ORC_ERR_OOM;
+    int rc = (ps.h && ps.hb && ps.start && ps.owner && ps.heap) ? ORC_OK : ORC_ERR_OOM;
     uint64_t ev_total = 0;
     while (rc == ORC_OK) {
         pthread_mutex_lock(&bp->lock);
@@ -565,10 +617,12 @@ static void *build_worker(void *arg) {
         if (stop || p >= m->L.P) break;
         ps.cnt = bp->part_start[p + 1] - bp->part_start[p];
         memcpy(ps.h, bp->by_part + bp->part_start[p], ps.cnt * sizeof(uint64_t));
+        if (bp->by_part_hi) memcpy(ps.hb, bp->by_part_hi + bp->part_start[p], ps.cnt * sizeof(uint64_t));
         uint64_t ev = 0;
         rc = build_part(bp->bc, &ps, p, m->pilots + p * m->L.B, bp->taken, &ev);
         ev_total += ev;
     }
+    if (ps.hb != ps.h) free(ps.hb);
     free(ps.h); free(ps.start); free(ps.owner); free(ps.heap);
     pthread_mutex_lock(&bp->lock);
     if (rc != ORC_OK && bp->rc == ORC_OK) bp->rc = rc;
@@ -650,32 +704,41 @@ static int build_common(const uint64_t *keys, const uint8_t *bytes, const uint64
     if (rc != ORC_OK) return rc;
     if (L.B > 0xFFFFFFFEull) return ORC_ERR_ARG;
 
+    /* Byte keys take the 128-bit hash beyond 2^32 keys, or when asked to
+     * (Sec. 3.1); u64 keys never need it (h = C k is injective). */
+    const int h128 = key_kind == ORC_KEY_BYTES && (prm->hash128 || n > (1ull << 32));
     uint64_t *h = (uint64_t *)malloc(n * sizeof(uint64_t));
     uint64_t *by_part = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint64_t *hh = h128 ? (uint64_t *)malloc(n * sizeof(uint64_t)) : NULL;
+    uint64_t *by_part_hi = h128 ? (uint64_t *)malloc(n * sizeof(uint64_t)) : NULL;
     uint64_t *part_start = (uint64_t *)calloc(L.P + 1, sizeof(uint64_t));
     uint64_t *cursor = (uint64_t *)calloc(L.P, sizeof(uint64_t));
     uint8_t *taken = (uint8_t *)calloc(L.P * L.S, 1);
-    if (!h || !by_part || !part_start || !cursor || !taken) {
-        free(h); free(by_part); free(part_start); free(cursor); free(taken);
+    if (!h || !by_part || !part_start || !cursor || !taken || (h128 && (!hh || !by_part_hi))) {
+        free(h); free(by_part); free(hh); free(by_part_hi); free(part_start); free(cursor); free(taken);
         return ORC_ERR_OOM;
     }
+    /* hb[i]: the hash that picks key i's part and bucket. */
+    const uint64_t *hb = h128 ? hh : h;
     g_total_evictions = 0;
     rc = ORC_ERR_BUILD;
     for (int attempt = 0; attempt <= prm->max_reseeds; attempt++) {
         uint64_t seed = prm->seed + (uint64_t)attempt;
         orc_mphf *m = (orc_mphf *)calloc(1, sizeof(orc_mphf));
         if (!m) { rc = ORC_ERR_OOM; break; }
-        m->L = L; m->gamma = prm->gamma; m->key_kind = key_kind;
+        m->L = L; m->gamma = prm->gamma; m->key_kind = key_kind; m->hash128 = h128;
         m->C = prm->C; m->seed = seed; m->lambda = prm->lambda; m->alpha = prm->alpha;
         m->pilots = (uint8_t *)calloc(L.P * L.B, 1);
         if (!m->pilots) { orc_free(m); rc = ORC_ERR_OOM; break; }
 
-        for (uint64_t i = 0; i < n; i++)
-            h[i] = key_kind == ORC_KEY_U64 ? orc_hash_u64(prm->C, keys[i])
-                                           : orc_hash_bytes(bytes + offsets[i], offsets[i + 1] - offsets[i], seed);
+        for (uint64_t i = 0; i < n; i++) {
+            if (key_kind == ORC_KEY_U64) h[i] = orc_hash_u64(prm->C, keys[i]);
+            else if (h128) orc_hash_bytes128(bytes + offsets[i], offsets[i + 1] - offsets[i], seed, &hh[i], &h[i]);
+            else h[i] = orc_hash_bytes(bytes + offsets[i], offsets[i + 1] - offsets[i], seed);
+        }
         /* Counting sort of the hashes by part. */
         memset(part_start, 0, (L.P + 1) * sizeof(uint64_t));
-        for (uint64_t i = 0; i < n; i++) part_start[orc_hi(L.P, h[i]) + 1]++;
+        for (uint64_t i = 0; i < n; i++) part_start[orc_hi(L.P, hb[i]) + 1]++;
         for (uint64_t p = 0; p < L.P; p++) part_start[p + 1] += part_start[p];
         int overfull = 0;
         for (uint64_t p = 0; p < L.P; p++) if (part_start[p + 1] - part_start[p] > L.S) overfull = 1;
@@ -686,13 +749,17 @@ static int build_common(const uint64_t *keys, const uint8_t *bytes, const uint64
             continue;
         }
         for (uint64_t p = 0; p < L.P; p++) cursor[p] = part_start[p];
-        for (uint64_t i = 0; i < n; i++) by_part[cursor[orc_hi(L.P, h[i])]++] = h[i];
+        for (uint64_t i = 0; i < n; i++) {
+            const uint64_t at = cursor[orc_hi(L.P, hb[i])]++;
+            by_part[at] = h[i];
+            if (h128) by_part_hi[at] = hh[i];
+        }
         memset(taken, 0, L.P * L.S);
 
         build_ctx bc = {m, prm->evict_mult};   /* 0: pure greedy, no eviction allowed */
         build_pool bp;
         memset(&bp, 0, sizeof(bp));
-        bp.bc = &bc; bp.by_part = by_part; bp.part_start = part_start; bp.taken = taken;
+        bp.bc = &bc; bp.by_part = by_part; bp.by_part_hi = by_part_hi; bp.part_start = part_start; bp.taken = taken;
         bp.rc = ORC_OK;
         pthread_mutex_init(&bp.lock, NULL);
         int threads = prm->threads < 1 ? 1 : (prm->threads > 256 ? 256 : prm->threads);
@@ -713,7 +780,7 @@ static int build_common(const uint64_t *keys, const uint8_t *bytes, const uint64
         if (rc == ORC_ERR_DUP_KEYS && key_kind == ORC_KEY_U64) break;  /* h = C*k: true duplicates */
         /* ORC_ERR_BUILD, or equal string hashes: try the next seed. */
     }
-    free(h); free(by_part); free(part_start); free(cursor); free(taken);
+    free(h); free(by_part); free(hh); free(by_part_hi); free(part_start); free(cursor); free(taken);
     return rc;
 }
 
@@ -737,7 +804,8 @@ void orc_free(orc_mphf *m) {
 /* ------------------------------------------------------------------ */
 /* 128-byte header:
  *   0 magic "PTRHASH1" | 8 u32 version=1 | 12 u32 key_kind | 16 u32 gamma
- *  20 u32 remap | 24 u32 reduce | 28 u32 0 | 32 u64 n | 40 u64 P | 48 u64 S
+ *  20 u32 remap | 24 u32 reduce | 28 u32 flags (bit 0: 128-bit string hash)
+ *  32 u64 n | 40 u64 P | 48 u64 S
  *  56 u64 B | 64 u64 C | 72 u64 seed | 80 u64 remap_len | 88 u64 remap_bytes
  *  96 f64 lambda | 104 f64 alpha | 112 u64 pilot_bytes (=P*B) | 120 u64 0
  * then the pilots (P*B bytes) zero-padded to a multiple of 64, then the
@@ -766,6 +834,7 @@ int orc_serialize(const orc_mphf *m, uint8_t *buf, uint64_t cap) {
     put_u32(buf + 16, (uint32_t)m->gamma);
     put_u32(buf + 20, (uint32_t)m->remap);
     put_u32(buf + 24, (uint32_t)m->L.reduce);
+    put_u32(buf + 28, m->hash128 ? 1u : 0u);
     put_u64(buf + 32, m->L.n);
     put_u64(buf + 40, m->L.P);
     put_u64(buf + 48, m->L.S);
@@ -796,6 +865,8 @@ int orc_deserialize(const uint8_t *buf, uint64_t len, orc_mphf **out) {
     m->gamma = (int)get_u32(buf + 16);
     m->remap = (int)get_u32(buf + 20);
     m->L.reduce = (int)get_u32(buf + 24);
+    const uint32_t flags = get_u32(buf + 28);
+    m->hash128 = (int)(flags & 1u);
     m->L.n = get_u64(buf + 32);
     m->L.P = get_u64(buf + 40);
     m->L.S = get_u64(buf + 48);
@@ -811,7 +882,8 @@ int orc_deserialize(const uint8_t *buf, uint64_t len, orc_mphf **out) {
               (m->remap != ORC_REMAP_CLEF && m->remap != ORC_REMAP_VEC) ||
               (m->L.reduce != ORC_REDUCE_POW2 && m->L.reduce != ORC_REDUCE_MOD) ||
               m->L.n == 0 || m->L.P == 0 || m->L.S == 0 || m->L.B == 0 ||
-              m->L.n > ORC_MAX_KEYS || m->L.S > 0xFFFFFFFFull ||
+              m->L.n > ORC_MAX_KEYS || m->L.S > 0xFFFFFFFFull || flags > 1u ||
+              (m->hash128 && m->key_kind != ORC_KEY_BYTES) ||
               pb != m->L.P * m->L.B || m->L.P * m->L.S < m->L.n ||
               m->remap_len != m->L.P * m->L.S - m->L.n ||
               (m->L.reduce == ORC_REDUCE_POW2 && !is_pow2(m->L.S));

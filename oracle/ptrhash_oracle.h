@@ -74,13 +74,14 @@ typedef struct {
     int32_t  max_reseeds;     /* reseed attempts after a failed part        */
     uint32_t evict_mult;      /* eviction cap = evict_mult * S per part     */
     int32_t  threads;         /* worker threads for independent parts       */
-    int32_t  pad;
+    int32_t  hash128;         /* byte keys: 1 = 128-bit hash; 0 = only when
+                                 n > 2^32 (Sec. 3.1, "Hash functions")       */
 } orc_params;
 
 /* Constructed structure, host memory. */
 typedef struct {
     orc_layout L;
-    int32_t  gamma, remap, key_kind, pad;
+    int32_t  gamma, remap, key_kind, hash128;
     uint64_t C, seed;
     double   lambda, alpha;
     uint8_t *pilots;        /* P*B bytes                                   */
@@ -99,6 +100,10 @@ uint64_t orc_hash_u64(uint64_t C, uint64_t k);
  * project's own definition (the paper's GxHash is not specified in it); it
  * is pinned only by structural properties in the tests. */
 uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed);
+/* The 128-bit variant: *lo is orc_hash_bytes, *hi the same construction
+ * with its own seed tweak and fold constant.  hi picks the part and bucket,
+ * lo the slot. */
+void     orc_hash_bytes128(const uint8_t *s, uint64_t len, uint64_t seed, uint64_t *hi, uint64_t *lo);
 uint64_t orc_hp(uint64_t C, uint64_t seed, uint64_t pilot);
 uint64_t orc_reduce(int reduce, uint64_t C, uint64_t x, uint64_t S);
 void     orc_part_bucket(const orc_layout *L, int gamma, uint64_t h,
@@ -122,6 +127,8 @@ void orc_free(orc_mphf *m);
 
 /* ---- query (one key at a time) ---- */
 uint64_t orc_slot_of_hash(const orc_mphf *m, uint64_t h);
+/* With separate hashes for the part and bucket (hb) and the slot (hs). */
+uint64_t orc_slot_of_hash2(const orc_mphf *m, uint64_t hb, uint64_t hs);
 uint64_t orc_query_hash(const orc_mphf *m, uint64_t h);
 void orc_query_u64_many(const orc_mphf *m, const uint64_t *keys, uint64_t cnt,
                         uint64_t *out, int threads);

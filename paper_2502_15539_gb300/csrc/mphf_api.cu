@@ -186,6 +186,7 @@ int mphf_serialize(const mphf_t *m, void *host_buf, size_t cap, size_t *needed) 
     wr32(b + 16, (uint32_t)h.gamma);
     wr32(b + 20, (uint32_t)h.remap);
     wr32(b + 24, (uint32_t)h.reduce);
+    wr32(b + 28, h.hash128 ? 1u : 0u);   // flags: bit 0 = 128-bit string hash
     wr64(b + 32, h.n); wr64(b + 40, h.P); wr64(b + 48, h.S); wr64(b + 56, h.B);
     wr64(b + 64, h.C); wr64(b + 72, h.seed);
     wr64(b + 80, h.remap_len); wr64(b + 88, h.remap_bytes);
@@ -236,6 +237,8 @@ static int parse_serialized(const uint8_t *b, size_t len, Header *out, uint64_t 
     h.gamma = (int32_t)rd32(b + 16);
     h.remap = (int32_t)rd32(b + 20);
     h.reduce = (int32_t)rd32(b + 24);
+    const uint32_t flags = rd32(b + 28);
+    h.hash128 = (int32_t)(flags & 1u);
     h.n = rd64(b + 32); h.P = rd64(b + 40); h.S = rd64(b + 48); h.B = rd64(b + 56);
     h.C = rd64(b + 64); h.seed = rd64(b + 72);
     h.remap_len = rd64(b + 80); h.remap_bytes = rd64(b + 88);
@@ -246,6 +249,7 @@ static int parse_serialized(const uint8_t *b, size_t len, Header *out, uint64_t 
                (h.gamma != MPHF_GAMMA_LINEAR && h.gamma != MPHF_GAMMA_CUBIC) ||
                (h.remap != MPHF_REMAP_CLEF && h.remap != MPHF_REMAP_VEC) ||
                (h.reduce != kReducePow2 && h.reduce != kReduceMod) ||
+               flags > 1u || (h.hash128 && h.key_kind != MPHF_KEY_BYTES) ||
                h.n == 0 || h.n > kMaxKeys || h.P == 0 || h.S == 0 || h.B == 0 ||
                h.S > 0xFFFFFFFFull || h.P > 0xFFFFFFFFull || h.B > 0xFFFFFFFFull ||
                pb != h.P * h.B || h.P * h.S < h.n || h.P * h.S - h.n >= kMaxKeys ||
@@ -395,6 +399,7 @@ int mphf_device_view(const mphf_t *m, mphf_view_t *out) {
     out->barrett = h.reduce == kReduceMod ? barrett_constant(h.S) : 0;
     out->s_mask = h.S - 1;
     out->gamma = h.gamma; out->reduce = h.reduce; out->remap_kind = h.remap; out->key_kind = h.key_kind;
+    out->hash128 = h.hash128;
     return MPHF_OK;
 }
 

@@ -241,7 +241,10 @@ static int stage_requests(mphf_batch *b, uint8_t *hb, const mphf_request *reqs, 
             return MPHF_ERR_ARG;
         }
         const Header &h = handle_header(r.m);
-        if (wide_values(h.n)) { set_error("request %u: n > 2^32 (32-bit results)", i); return MPHF_ERR_ARG; }
+        if (wide_values(h.n) || h.hash128) {
+            set_error("request %u: n > 2^32 or a 128-bit string hash (use mphf_query_*_wide)", i);
+            return MPHF_ERR_ARG;
+        }
         if ((h.key_kind == MPHF_KEY_BYTES) != (r.offsets_dev != nullptr)) {
             set_error("request %u: offsets must be given exactly for byte-key structures", i);
             return MPHF_ERR_ARG;

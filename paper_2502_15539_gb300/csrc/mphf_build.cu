@@ -49,18 +49,21 @@ __device__ __forceinline__ uint64_t global_bucket(uint64_t h, uint64_t P, uint64
     return part * B + mul_hi(B, bucket_fn<GAMMA>(P * h));
 }
 
-// The n sorted hashes all lie in global buckets [gb_lo, gb_hi); bstart[b -
-// gb_lo] = index of the first of them in bucket b, for gb_lo <= b <= gb_hi.
+// The n sorted bucket hashes all lie in global buckets [gb_lo, gb_hi);
+// bstart[b - gb_lo] = index of the first of them in bucket b, for gb_lo <= b
+// <= gb_hi.  With 128-bit hashes, sorted_lo holds the low halves (the keys
+// are sorted by (high, low)) and a duplicate is an equal pair.
 template <int GAMMA>
-__global__ void bucket_bounds_kernel(const uint64_t *__restrict__ sorted, uint64_t n, uint64_t P, uint64_t B,
-                                     uint64_t gb_lo, uint64_t gb_hi, uint32_t *__restrict__ bstart,
-                                     uint32_t *__restrict__ dup) {
+__global__ void bucket_bounds_kernel(const uint64_t *__restrict__ sorted, const uint64_t *__restrict__ sorted_lo,
+                                     uint64_t n, uint64_t P, uint64_t B, uint64_t gb_lo, uint64_t gb_hi,
+                                     uint32_t *__restrict__ bstart, uint32_t *__restrict__ dup) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t hi_b = i < n ? global_bucket<GAMMA>(sorted[i], P, B) : gb_hi;
         const uint64_t lo_b = i > 0 ? global_bucket<GAMMA>(sorted[i - 1], P, B) + 1 : gb_lo;
         for (uint64_t b = lo_b; b <= hi_b; b++) bstart[b - gb_lo] = (uint32_t)i;
-        if (i > 0 && i < n && sorted[i] == sorted[i - 1]) *dup = 1;
+        if (i > 0 && i < n && sorted[i] == sorted[i - 1] && (!sorted_lo || sorted_lo[i] == sorted_lo[i - 1]))
+            *dup = 1;
     }
 }
 
@@ -74,27 +77,30 @@ __global__ void part_size_kernel(const uint32_t *__restrict__ bstart, uint64_t n
 // One shard of the keys: the hashes of the keys whose part lies in
 // [part_lo, part_hi), appended in any order (they are sorted next).  At
 // most `cap` are stored; more raise *overflow (some part then holds more
-// than S keys).  h = C k for u64 keys, the string hash for byte keys.
+// than S keys).  h = C k for u64 keys, the string hash for byte keys; with
+// out_hi, the 128-bit string hash, whose high half (out_hi) picks the part.
 __global__ void shard_hash_kernel(int key_kind, const void *__restrict__ keys, const uint64_t *__restrict__ offsets,
                                   uint64_t n, uint64_t C, uint64_t seed, uint64_t P, uint64_t part_lo,
-                                  uint64_t part_hi, uint64_t *__restrict__ out, uint64_t cap,
-                                  unsigned long long *__restrict__ count, uint32_t *__restrict__ overflow) {
+                                  uint64_t part_hi, uint64_t *__restrict__ out, uint64_t *__restrict__ out_hi,
+                                  uint64_t cap, unsigned long long *__restrict__ count,
+                                  uint32_t *__restrict__ overflow) {
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     // Every lane of a warp runs the same number of iterations.
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     for (uint64_t w = first; w < n; w += stride) {
         const uint64_t i = w + lane;
-        uint64_t h = 0;
+        uint64_t h[2] = {0, 0};
         bool keep = false;
         if (i < n) {
             if (key_kind == MPHF_KEY_U64) {
-                h = C * __ldg(static_cast<const uint64_t *>(keys) + i);
+                h[0] = C * __ldg(static_cast<const uint64_t *>(keys) + i);
             } else {
                 const uint64_t a = __ldg(offsets + i), e = __ldg(offsets + i + 1);
-                h = hash_string_global(static_cast<const uint8_t *>(keys), a, e - a, seed);
+                if (out_hi) hash_string_global_n<true>(static_cast<const uint8_t *>(keys), a, e - a, seed, h);
+                else hash_string_global_n<false>(static_cast<const uint8_t *>(keys), a, e - a, seed, h);
             }
-            const uint64_t part = mul_hi(P, h);
+            const uint64_t part = mul_hi(P, out_hi ? h[1] : h[0]);
             keep = part >= part_lo && part < part_hi;
         }
         const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
@@ -104,8 +110,12 @@ __global__ void shard_hash_kernel(int key_kind, const void *__restrict__ keys, c
         base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
         if (keep) {
             const uint64_t j = base + __popc(m & ((1u << lane) - 1));
-            if (j < cap) out[j] = h;
-            else *overflow = 1;
+            if (j < cap) {
+                out[j] = h[0];
+                if (out_hi) out_hi[j] = h[1];
+            } else {
+                *overflow = 1;
+            }
         }
     }
 }
@@ -821,9 +831,17 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     const uint64_t cap = shards == 1 ? n : max_parts * S;    // hashes a valid shard can hold
     if (cap > kMaxShardKeys) { set_error("%llu keys in one shard", (unsigned long long)cap); return MPHF_ERR_CAPACITY; }
     const unsigned search_grid = (unsigned)(max_parts < (uint64_t)sms ? max_parts : (uint64_t)sms);
-    DevBuf hash, sorted, bstart, pilots, taken, owner, order, ohash, status, flags, cub_tmp;
+    // Byte keys take the 128-bit hash beyond 2^32 keys or when asked to
+    // (Sec. 3.1): its high half picks part and bucket, its low half the slot,
+    // and the keys are sorted by (high, low) with two stable radix passes.
+    const bool h128 = key_kind == MPHF_KEY_BYTES && (prm.hash128 != 0 || n > (1ull << 32));
+    DevBuf hash, sorted, hash_hi, sorted_hi, bstart, pilots, taken, owner, order, ohash, status, flags, cub_tmp;
     CK(hash.alloc(cap * 8));
     CK(sorted.alloc(cap * 8));
+    if (h128) {
+        CK(hash_hi.alloc(cap * 8));
+        CK(sorted_hi.alloc(cap * 8));
+    }
     CK(bstart.alloc((max_parts * B + 1) * 4));
     CK(pilots.alloc((nbkt + 63) & ~63ull));
     CK(taken.alloc((words + 1) * 4));
@@ -833,7 +851,11 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     CK(status.alloc(P * 4));
     CK(flags.alloc(64));
     size_t sort_tmp = 0;
-    CK(cub::DeviceRadixSort::SortKeys(nullptr, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), cap, 0, 64, s));
+    if (h128)
+        CK(cub::DeviceRadixSort::SortPairs(nullptr, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(),
+                                           hash_hi.as<uint64_t>(), sorted_hi.as<uint64_t>(), cap, 0, 64, s));
+    else
+        CK(cub::DeviceRadixSort::SortKeys(nullptr, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), cap, 0, 64, s));
     CK(cub_tmp.alloc(sort_tmp));
     // [0] dup, [1] overfull, [2] next part, [3] span, [4..5] evictions, [6] shard overflow, [8..9] shard count
     uint32_t *d_flags = flags.as<uint32_t>();
@@ -842,6 +864,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     Header h;
     h.n = n; h.P = P; h.S = S; h.B = B; h.C = prm.C; h.gamma = prm.gamma; h.reduce = reduce;
     h.key_kind = key_kind; h.lambda = prm.lambda; h.alpha = prm.alpha; h.remap_len = total - n;
+    h.hash128 = h128 ? 1 : 0;
     uint64_t evictions_total = 0;
     bool built = false;
     int last_fail = MPHF_ERR_BUILD_FAILED;
@@ -857,11 +880,13 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
             CK(cudaMemsetAsync(d_flags, 0, 64, s));
             uint64_t m = n;
             if (shards == 1) {
-                rc = launch_hash_keys(key_kind, keys, offsets, n, prm.C, seed, hash.as<uint64_t>(), sms, s);
+                rc = launch_hash_keys(key_kind, keys, offsets, n, prm.C, seed, hash.as<uint64_t>(),
+                                      h128 ? hash_hi.as<uint64_t>() : nullptr, sms, s);
                 if (rc) return rc;
             } else {
                 shard_hash_kernel<<<grid_for(n, sms), 256, 0, s>>>(
-                    key_kind, keys, offsets, n, prm.C, seed, P, p_lo, p_hi, hash.as<uint64_t>(), cap,
+                    key_kind, keys, offsets, n, prm.C, seed, P, p_lo, p_hi, hash.as<uint64_t>(),
+                    h128 ? hash_hi.as<uint64_t>() : nullptr, cap,
                     reinterpret_cast<unsigned long long *>(d_flags + 8), d_flags + 6);
                 count_launch();
                 CK(cudaGetLastError());
@@ -872,16 +897,30 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
                 if (fl[0]) m = cap + 1;   // too many keys for the shard's parts: reported below as overfull
             }
             uint32_t hf[2] = {0, 0};
+            // slot_h: the sorted slot hashes the search reads; bucket_h: the
+            // sorted hashes that pick part and bucket (the same array unless 128-bit).
+            const uint64_t *slot_h = sorted.as<uint64_t>(), *bucket_h = sorted.as<uint64_t>();
             if (m <= cap) {
-                CK(cub::DeviceRadixSort::SortKeys(cub_tmp.p, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), m, 0, 64, s));
-                count_launch(4);
+                if (h128) {   // by low half, then stably by high half: sorted by (high, low)
+                    CK(cub::DeviceRadixSort::SortPairs(cub_tmp.p, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(),
+                                                       hash_hi.as<uint64_t>(), sorted_hi.as<uint64_t>(), m, 0, 64, s));
+                    CK(cub::DeviceRadixSort::SortPairs(cub_tmp.p, sort_tmp, sorted_hi.as<uint64_t>(), hash_hi.as<uint64_t>(),
+                                                       sorted.as<uint64_t>(), hash.as<uint64_t>(), m, 0, 64, s));
+                    count_launch(8);
+                    slot_h = hash.as<uint64_t>();
+                    bucket_h = hash_hi.as<uint64_t>();
+                } else {
+                    CK(cub::DeviceRadixSort::SortKeys(cub_tmp.p, sort_tmp, hash.as<uint64_t>(), sorted.as<uint64_t>(), m, 0, 64, s));
+                    count_launch(4);
+                }
                 const uint64_t gb_lo = p_lo * B, gb_hi = p_hi * B;
+                const uint64_t *dup_lo = h128 ? slot_h : nullptr;
                 if (prm.gamma == MPHF_GAMMA_CUBIC)
                     bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(m + 1, sms), 256, 0, s>>>(
-                        sorted.as<uint64_t>(), m, P, B, gb_lo, gb_hi, bstart.as<uint32_t>(), d_flags);
+                        bucket_h, dup_lo, m, P, B, gb_lo, gb_hi, bstart.as<uint32_t>(), d_flags);
                 else
                     bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(m + 1, sms), 256, 0, s>>>(
-                        sorted.as<uint64_t>(), m, P, B, gb_lo, gb_hi, bstart.as<uint32_t>(), d_flags);
+                        bucket_h, dup_lo, m, P, B, gb_lo, gb_hi, bstart.as<uint32_t>(), d_flags);
                 part_size_kernel<<<grid_for(p_hi - p_lo, sms), 256, 0, s>>>(bstart.as<uint32_t>(), p_hi - p_lo, B, S, d_flags + 1);
                 count_launch(2);
                 CK(cudaGetLastError());
@@ -905,7 +944,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
                 break;
             }
             SearchArgs a;
-            a.sorted = sorted.as<uint64_t>(); a.bstart = bstart.as<uint32_t>(); a.pilots = pilots.as<uint8_t>();
+            a.sorted = slot_h; a.bstart = bstart.as<uint32_t>(); a.pilots = pilots.as<uint8_t>();
             a.taken = taken.as<uint32_t>(); a.owner_scratch = owner.as<uint32_t>(); a.order_scratch = order.as<uint64_t>();
             a.ohash_scratch = ohash.as<uint64_t>();
             a.status = status.as<uint32_t>();
@@ -1138,14 +1177,14 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
         const uint64_t seed = prm.seed + (uint64_t)attempt;
         h.seed = seed;
         CK(cudaMemsetAsync(flags, 0, 64, s));
-        rc = launch_hash_keys(MPHF_KEY_U64, keys, nullptr, n, prm.C, seed, hash, sms, s);
+        rc = launch_hash_keys(MPHF_KEY_U64, keys, nullptr, n, prm.C, seed, hash, nullptr, sms, s);
         if (rc) return rc;
         CK(cub::DeviceRadixSort::SortKeys(sort_buf, sort_tmp, hash, sorted, n, 0, 64, s));
         count_launch(4);
         if (prm.gamma == MPHF_GAMMA_CUBIC)
-            bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, 0, P * B, bstart, flags);
+            bucket_bounds_kernel<MPHF_GAMMA_CUBIC><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, nullptr, n, P, B, 0, P * B, bstart, flags);
         else
-            bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, n, P, B, 0, P * B, bstart, flags);
+            bucket_bounds_kernel<MPHF_GAMMA_LINEAR><<<grid_for(n + 1, sms), 256, 0, s>>>(sorted, nullptr, n, P, B, 0, P * B, bstart, flags);
         part_size_kernel<<<grid_for(P, sms), 256, 0, s>>>(bstart, P, B, S, flags + 1);
         count_launch(2);
         CK(cudaGetLastError());

@@ -34,6 +34,7 @@ struct Header {
     uint64_t n = 0, P = 0, S = 0, B = 0, C = 0, seed = 0;
     int32_t gamma = MPHF_GAMMA_CUBIC, remap = MPHF_REMAP_CLEF, reduce = kReducePow2;
     int32_t key_kind = MPHF_KEY_U64;
+    int32_t hash128 = 0;       // byte keys hashed to 128 bits (high: part and bucket, low: slot)
     double lambda = 3.5, alpha = 0.99;
     uint64_t remap_len = 0;    // P*S - n
     uint64_t remap_bytes = 0;  // bytes of the remap payload
@@ -68,9 +69,10 @@ int launch_query_u64_wide(const Header &h, const View &v, const uint64_t *keys, 
 int launch_query_bytes_wide(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
                             uint64_t count, uint64_t *out, cudaStream_t s);
 
-// Key hashes for the builder (mphf_query.cu).
+// Key hashes for the builder (mphf_query.cu); out_hi (high halves of the
+// 128-bit string hash) may be NULL.
 int launch_hash_keys(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t C,
-                     uint64_t seed, uint64_t *out, int sm_count, cudaStream_t s);
+                     uint64_t seed, uint64_t *out, uint64_t *out_hi, int sm_count, cudaStream_t s);
 
 // Builder (mphf_build.cu).  Fills header, pilots and remap on the device.
 struct BuildResult {

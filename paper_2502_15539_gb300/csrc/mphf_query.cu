@@ -190,7 +190,7 @@ constexpr int kBlkStage = kStrThreads * 64 + 64;     // staged bytes per block
 // whole key buffer may be read; only the chunk crossing that end is read
 // byte by byte), then each thread hashes its string from the stage.  A
 // block whose bytes do not fit the stage hashes from global memory.
-template <int GAMMA, int REDUCE, int REMAP, bool WIDE>
+template <int GAMMA, int REDUCE, int REMAP, bool WIDE, bool H128>
 __global__ void __launch_bounds__(kStrThreads)
 query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                    const uint64_t count, void *__restrict__ out) {
@@ -221,23 +221,23 @@ query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64
         __syncthreads();
     }
     if (i >= count) return;
-    uint64_t h;
+    uint64_t h[2];   // [0] the slot hash; with H128, [1] the high half, which picks part and bucket
     if (staged) {
         const uint32_t st = (uint32_t)(a - base);
         const uint32_t *w = reinterpret_cast<const uint32_t *>(stage) + (st >> 2);
-        h = hash_string_words([&](uint32_t k) { return w[k]; }, 8 * (st & 3u), (uint32_t)(e - a), v.seed);
+        hash_string_words_n<H128>([&](uint32_t k) { return w[k]; }, 8 * (st & 3u), (uint32_t)(e - a), v.seed, h);
     } else {
-        h = hash_string_global(bytes, a, e - a, v.seed);
+        hash_string_global_n<H128>(bytes, a, e - a, v.seed, h);
     }
     uint64_t part;
-    const uint64_t b = bucket_of<GAMMA>(v, h, part);
+    const uint64_t b = bucket_of<GAMMA>(v, H128 ? h[1] : h[0], part);
     const uint32_t p = __ldg(v.pilots + b);
-    if constexpr (WIDE) static_cast<uint64_t *>(out)[i] = slot_value_wide<REDUCE, REMAP>(v, h, part, p);
-    else static_cast<uint32_t *>(out)[i] = slot_value<REDUCE, REMAP, false>(v, h, part, p);
+    if constexpr (WIDE) static_cast<uint64_t *>(out)[i] = slot_value_wide<REDUCE, REMAP>(v, h[0], part, p);
+    else static_cast<uint32_t *>(out)[i] = slot_value<REDUCE, REMAP, false>(v, h[0], part, p);
 }
 
 template <int GAMMA, int REDUCE, int REMAP, bool WIDE>
-static int launch_bytes_t(const View &v, const uint8_t *bytes, const uint64_t *offsets, uint64_t count,
+static int launch_bytes_t(const View &v, bool h128, const uint8_t *bytes, const uint64_t *offsets, uint64_t count,
                           void *out, cudaStream_t s) {
     const uint64_t blocks = (count + kStrThreads - 1) / kStrThreads;
     if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
@@ -245,7 +245,10 @@ static int launch_bytes_t(const View &v, const uint8_t *bytes, const uint64_t *o
         set_error("byte keys need a 16-byte aligned buffer");
         return MPHF_ERR_ARG;
     }
-    query_bytes_kernel<GAMMA, REDUCE, REMAP, WIDE><<<(unsigned)blocks, kStrThreads, 0, s>>>(v, bytes, offsets, count, out);
+    if (h128)
+        query_bytes_kernel<GAMMA, REDUCE, REMAP, WIDE, true><<<(unsigned)blocks, kStrThreads, 0, s>>>(v, bytes, offsets, count, out);
+    else
+        query_bytes_kernel<GAMMA, REDUCE, REMAP, WIDE, false><<<(unsigned)blocks, kStrThreads, 0, s>>>(v, bytes, offsets, count, out);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "query_bytes launch");
@@ -255,10 +258,10 @@ template <bool WIDE>
 static int dispatch_bytes(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
                           uint64_t count, void *out, cudaStream_t s) {
     const bool cubic = h.gamma == MPHF_GAMMA_CUBIC, pow2 = h.reduce == kReducePow2;
-    const bool vec = h.remap == MPHF_REMAP_VEC;
+    const bool vec = h.remap == MPHF_REMAP_VEC, h128 = h.hash128 != 0;
 #define MPHF_BYTES_CASE(G, R)                                                                  \
-    return vec ? launch_bytes_t<G, R, kRemapVec, WIDE>(v, bytes, offsets, count, out, s)     \
-               : launch_bytes_t<G, R, kRemapClef, WIDE>(v, bytes, offsets, count, out, s);
+    return vec ? launch_bytes_t<G, R, kRemapVec, WIDE>(v, h128, bytes, offsets, count, out, s)     \
+               : launch_bytes_t<G, R, kRemapClef, WIDE>(v, h128, bytes, offsets, count, out, s);
     if (cubic && pow2) { MPHF_BYTES_CASE(MPHF_GAMMA_CUBIC, kReducePow2) }
     if (cubic) { MPHF_BYTES_CASE(MPHF_GAMMA_CUBIC, kReduceMod) }
     if (pow2) { MPHF_BYTES_CASE(MPHF_GAMMA_LINEAR, kReducePow2) }
@@ -280,23 +283,30 @@ int launch_query_bytes_wide(const Header &h, const View &v, const uint8_t *bytes
 // for byte keys (one thread per key).
 __global__ void hash_keys_kernel(int key_kind, const void *__restrict__ keys,
                                  const uint64_t *__restrict__ offsets, uint64_t n, uint64_t C,
-                                 uint64_t seed, uint64_t *__restrict__ out) {
+                                 uint64_t seed, uint64_t *__restrict__ out, uint64_t *__restrict__ out_hi) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         if (key_kind == MPHF_KEY_U64) {
             out[i] = C * __ldg(static_cast<const uint64_t *>(keys) + i);
         } else {
             const uint64_t a = __ldg(offsets + i), e = __ldg(offsets + i + 1);
-            out[i] = hash_string_global(static_cast<const uint8_t *>(keys), a, e - a, seed);
+            uint64_t h[2];
+            if (out_hi) {
+                hash_string_global_n<true>(static_cast<const uint8_t *>(keys), a, e - a, seed, h);
+                out_hi[i] = h[1];
+            } else {
+                hash_string_global_n<false>(static_cast<const uint8_t *>(keys), a, e - a, seed, h);
+            }
+            out[i] = h[0];
         }
     }
 }
 
 int launch_hash_keys(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t C,
-                     uint64_t seed, uint64_t *out, int sm_count, cudaStream_t s) {
+                     uint64_t seed, uint64_t *out, uint64_t *out_hi, int sm_count, cudaStream_t s) {
     const uint64_t want = (n + 255) / 256;
     const unsigned blocks = (unsigned)(want < (uint64_t)sm_count * 16 ? (want ? want : 1) : (uint64_t)sm_count * 16);
-    hash_keys_kernel<<<blocks, 256, 0, s>>>(key_kind, keys, offsets, n, C, seed, out);
+    hash_keys_kernel<<<blocks, 256, 0, s>>>(key_kind, keys, offsets, n, C, seed, out, out_hi);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "hash keys launch");

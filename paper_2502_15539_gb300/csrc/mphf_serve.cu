@@ -408,7 +408,10 @@ int mphf_server_add(mphf_server_t *s, const void *serialized, size_t len, uint32
     uint64_t n = 0;
     int rc = ptrhash::serialized_device_bytes(serialized, len, &e.dev_bytes, &n);
     if (rc) return rc;
-    if (ptrhash::wide_values(n)) { ptrhash::set_error("n > 2^32: the server returns 32-bit results"); return MPHF_ERR_ARG; }
+    if (ptrhash::wide_values(n) || ((const uint8_t *)serialized)[28] & 1u) {
+        ptrhash::set_error("n > 2^32 or a 128-bit string hash: not served (32-bit batched queries)");
+        return MPHF_ERR_ARG;
+    }
     if (e.dev_bytes > s->arena.cap) {
         ptrhash::set_error("structure of %llu bytes exceeds the HBM budget", (unsigned long long)e.dev_bytes);
         return MPHF_ERR_CAPACITY;

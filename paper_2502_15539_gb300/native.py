@@ -47,7 +47,8 @@ class mphf_params(ctypes.Structure):
                 ("gamma", ctypes.c_int32), ("remap", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("C", ctypes.c_uint64),
                 ("slots_override", ctypes.c_uint64), ("max_reseeds", ctypes.c_int32),
-                ("evict_mult", ctypes.c_uint32), ("shard_keys", ctypes.c_uint64)]
+                ("evict_mult", ctypes.c_uint32), ("shard_keys", ctypes.c_uint64),
+                ("hash128", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mphf_info_t(ctypes.Structure):
@@ -68,7 +69,7 @@ class mphf_view_t(ctypes.Structure):
                 ("P", ctypes.c_uint64), ("S", ctypes.c_uint64), ("B", ctypes.c_uint64), ("C", ctypes.c_uint64),
                 ("seed", ctypes.c_uint64), ("barrett", ctypes.c_uint64), ("s_mask", ctypes.c_uint64),
                 ("gamma", ctypes.c_int32), ("reduce", ctypes.c_int32), ("remap_kind", ctypes.c_int32),
-                ("key_kind", ctypes.c_int32)]
+                ("key_kind", ctypes.c_int32), ("hash128", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mphf_request(ctypes.Structure):

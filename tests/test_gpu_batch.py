@@ -113,3 +113,18 @@ def test_autotune_picks_a_valid_shape_and_caches_it(batch_set, tmp_path):
     assert b2.autotune(arr, len(items), str(cache)) == best           # read from the cache
     assert cache.read_text().count("keys_per_thread") == 1
     run_and_check(N, b2, structs, reqs)
+
+
+def test_batch_refuses_128_bit_string_structures():
+    """The batch executor returns 32-bit results through the 64-bit string
+    hash only; a structure with the 128-bit hash is refused, not misread."""
+    N = need_gpu()
+    ids = torch.arange(500)
+    data, off = W.strings(ids, seed=10)
+    ref = O.OracleMPHF.build_bytes(data.numpy(), off.numpy().astype(np.uint64), hash128=1)
+    m = N.mphf_deserialize(ref.serialize())
+    out = torch.full((500,), -1, dtype=torch.int32, device="cuda")
+    arr, keep = N.make_requests([(m, data.cuda(), off.cuda(), out)])
+    with pytest.raises(N.MphfError) as e:
+        N.Batch(4).run(arr, 1)
+    assert e.value.code == N.MPHF_ERR_ARG

