@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MPHF ns/key & queries/s at n=1e9 u64; % of random-gather roofline; p99 lat"
 UNIT = "queries/s"
-QUERY_KERNEL_SOURCES = ["paper_2502_15539_gb300/csrc/mphf_query.cu", "paper_2502_15539_gb300/csrc/mphf_internal.cuh"]
+QUERY_KERNEL_SOURCES = ["paper_2502_15539_gb300/csrc/mphf_query.cu", "paper_2502_15539_gb300/csrc/mphf_internal.cuh",
+                        "include/mphf_device.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "query_u64_kernel_n1e9.md")
 
 
