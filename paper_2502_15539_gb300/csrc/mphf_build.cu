@@ -206,42 +206,49 @@ __device__ __forceinline__ bool in_recent(const uint32_t *recent, uint32_t b) {
 // myh is key `lane`'s hash (lanes >= s hold anything).
 template <int REDUCE>
 __device__ int greedy_small(const SearchArgs &a, const uint32_t *bits, uint64_t myh, int s, int lane) {
+    // s is warp-uniform, so the loops below stop at s for the whole warp
+    // (the shuffles included) and sl stays in registers.
     for (int r = 0; r < 8; r++) {
         const uint64_t hp = a.C * ((uint64_t)(32 * r + lane) ^ a.seed);
         uint32_t sl[kSmallBucket];
         bool ok = true;
 #pragma unroll
         for (int j = 0; j < kSmallBucket; j++) {
-            const uint64_t hj = __shfl_sync(0xFFFFFFFFu, myh, j);
-            if (j < s) {
-                sl[j] = slot_in_part<REDUCE>(a, hj ^ hp);
-                ok &= !bit_of(bits, sl[j]);
-            }
+            if (j >= s) break;
+            sl[j] = slot_in_part<REDUCE>(a, __shfl_sync(0xFFFFFFFFu, myh, j) ^ hp);
+            ok &= !bit_of(bits, sl[j]);
+#pragma unroll
+            for (int k = 0; k < j; k++) ok &= sl[j] != sl[k];
         }
-#pragma unroll
-        for (int j = 1; j < kSmallBucket; j++)
-#pragma unroll
-            for (int k = 0; k < j; k++)
-                if (j < s && sl[j] == sl[k]) ok = false;
         const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
         if (m) return 32 * r + __ffs(m) - 1;
     }
     return -1;
 }
 
-// Key-parallel greedy search for a large bucket: pilots in increasing order,
-// lanes over the keys, self-collisions found through the slot set.
+// Greedy search for a large bucket (hashes in sh.hcache).  Lane l tries
+// pilot 32 r + l against the taken slots, key after key, until every lane
+// has hit a taken slot; the surviving pilots, smallest first, are then
+// checked for self-collisions key-parallel through the slot set.  The
+// result is the smallest pilot whose keys land on distinct free slots.
 template <int REDUCE>
 __device__ int greedy_large(const SearchArgs &a, const SearchShared &sh, int s, uint32_t &gen, int lane) {
-    for (int p = 0; p < 256; p++) {
-        const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
-        gen = bump_gen(gen, sh.set, lane);
-        bool bad = false;
-        for (int j = lane; j < s; j += 32) {
-            const uint32_t sl = slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp);
-            if (bit_of(sh.bits, sl) || !set_insert(sh.set, sl, gen)) bad = true;
+    for (int r = 0; r < 8; r++) {
+        const uint64_t hp = a.C * ((uint64_t)(32 * r + lane) ^ a.seed);
+        bool ok = true;
+        for (int j = 0; j < s; j++) {
+            if ((j & 3) == 0 && !__any_sync(0xFFFFFFFFu, ok)) break;
+            if (ok) ok = !bit_of(sh.bits, slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp));
         }
-        if (!__any_sync(0xFFFFFFFFu, bad)) return p;
+        for (unsigned m = __ballot_sync(0xFFFFFFFFu, ok); m; m &= m - 1) {
+            const int p = 32 * r + __ffs(m) - 1;
+            const uint64_t hpc = a.C * ((uint64_t)p ^ a.seed);
+            gen = bump_gen(gen, sh.set, lane);
+            bool bad = false;
+            for (int j = lane; j < s; j += 32)
+                if (!set_insert(sh.set, slot_in_part<REDUCE>(a, sh.hcache[j] ^ hpc), gen)) bad = true;
+            if (!__any_sync(0xFFFFFFFFu, bad)) return p;
+        }
     }
     return -1;
 }
@@ -263,27 +270,26 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
         for (int r = 0; r < 8; r++) {
             const int p = 32 * r + lane;
             const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
-            uint32_t sl[kSmallBucket];
+            uint32_t sl[kSmallBucket], oe[kSmallBucket];
             bool ok = true;
             uint64_t cost = 0;
+            // Slots first and every owner load issued before any is used.
 #pragma unroll
             for (int j = 0; j < kSmallBucket; j++) {
-                const uint64_t hj = __shfl_sync(0xFFFFFFFFu, myh, j);
-                if (j < s) {
-                    sl[j] = slot_in_part<REDUCE>(a, hj ^ hp);
-                    if (bit_of(sh.bits, sl[j])) {
-                        const uint32_t oe = owner[sl[j]];
-                        if (use_tabu && in_recent(sh.recent, oe & kOwnerMask)) ok = false;
-                        const uint64_t z = oe >> kOwnerShift;
-                        cost += z * z;
-                    }
-                }
+                if (j >= s) break;
+                sl[j] = slot_in_part<REDUCE>(a, __shfl_sync(0xFFFFFFFFu, myh, j) ^ hp);
+                oe[j] = bit_of(sh.bits, sl[j]) ? owner[sl[j]] : kNone;
+#pragma unroll
+                for (int k = 0; k < j; k++) ok &= sl[j] != sl[k];
             }
 #pragma unroll
-            for (int j = 1; j < kSmallBucket; j++)
-#pragma unroll
-                for (int k = 0; k < j; k++)
-                    if (j < s && sl[j] == sl[k]) ok = false;
+            for (int j = 0; j < kSmallBucket; j++) {
+                if (j >= s) break;
+                if (oe[j] == kNone) continue;
+                if (use_tabu && in_recent(sh.recent, oe[j] & kOwnerMask)) ok = false;
+                const uint64_t z = oe[j] >> kOwnerShift;
+                cost += z * z;
+            }
             uint64_t c = ok ? cost : ~0ull;
             int pp = ok ? p : 0x7FFFFFFF;
             for (int off = 16; off; off >>= 1) {
@@ -331,8 +337,8 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
     if (np > (uint32_t)kPendingCap) return kPartPendingFull;
     uint32_t wbase = kNone;          // first position held in the descriptor window
     uint64_t wdesc = 0;              // lane l: descriptor of position wbase + l
-    uint32_t pf_pos = kNone;         // position whose hashes were prefetched
-    uint64_t pf_h = 0;
+    uint32_t pf_pos = kNone;         // position whose first 64 hashes were prefetched
+    uint64_t pf_h = 0, pf_h2 = 0;    // lane l: hashes l and l + 32
     for (int i = lane; i < 16; i += 32) sh.recent[i] = kNone;
     for (int i = lane; i < kSetSize; i += 32) sh.set[i] = 0;
     __syncwarp();
@@ -375,9 +381,14 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
             b = (uint32_t)od;
             s = (int)ord_z;
             const uint64_t koff = od >> 44;
-            myh = (pf_pos == next) ? pf_h : (lane < s ? ohash[koff + lane] : 0);
-            if (s > kSmallBucket) {
-                for (int j = lane; j < s; j += 32) sh.hcache[j] = ohash[koff + j];
+            const bool pf = pf_pos == next;
+            myh = pf ? pf_h : (lane < s ? ohash[koff + lane] : 0);
+            if (s > kSmallBucket) {   // the first 64 hashes may have been prefetched
+                if (pf) {
+                    if (lane < s) sh.hcache[lane] = pf_h;
+                    if (lane + 32 < s) sh.hcache[lane + 32] = pf_h2;
+                }
+                for (int j = (pf ? 64 : 0) + lane; j < s; j += 32) sh.hcache[j] = ohash[koff + j];
                 __syncwarp();
             }
             next++;
@@ -386,7 +397,8 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
             const uint64_t d2 = __shfl_sync(0xFFFFFFFFu, wdesc, (next - wbase) & 31);
             const uint32_t z2 = (uint32_t)(d2 >> 32) & 0xFFFu;
             pf_pos = next;
-            pf_h = (z2 <= (uint32_t)kSmallBucket && (uint32_t)lane < z2) ? ohash[(d2 >> 44) + lane] : 0;
+            pf_h = (uint32_t)lane < z2 ? ohash[(d2 >> 44) + lane] : 0;
+            pf_h2 = (uint32_t)lane + 32 < z2 ? ohash[(d2 >> 44) + lane + 32] : 0;
         } else {
             pf_pos = kNone;
         }
@@ -399,15 +411,38 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
             if (chosen < 0) chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, false);
             if (chosen < 0) { status = kPartNoPilot; break; }
             const uint64_t hp = a.C * ((uint64_t)chosen ^ a.seed);
+            // Up to 32 keys: lane j reads the owner of key j's slot, and that
+            // owner's first key and pilot, all at once.  While a slot's bit is
+            // still set its owner is the one read here (nothing is placed in
+            // this loop), so the evictions below use these values in key order.
+            uint32_t sl_l = 0, oe_l = kNone;
+            uint64_t ob_l = 0, ohp_l = 0;
+            if (s <= 32 && lane < s) {
+                sl_l = slot_in_part<REDUCE>(a, (s <= kSmallBucket ? myh : sh.hcache[lane]) ^ hp);
+                if (bit_of(sh.bits, sl_l)) {
+                    oe_l = owner[sl_l];
+                    const uint32_t o = oe_l & kOwnerMask;
+                    ob_l = a.bstart[gb0 - a.bbase + o];
+                    ohp_l = a.C * ((uint64_t)a.pilots[gb0 + o] ^ a.seed);
+                }
+            }
             for (int j = 0; j < s; j++) {
-                const uint64_t hj = s <= kSmallBucket ? __shfl_sync(0xFFFFFFFFu, myh, j) : sh.hcache[j];
-                const uint32_t sl = slot_in_part<REDUCE>(a, hj ^ hp);
-                if (!bit_of(sh.bits, sl)) continue;        // free, or its owner already evicted
-                const uint32_t oe = owner[sl];
-                const uint32_t o = oe & kOwnerMask;
+                uint32_t sl, oe;
+                uint64_t ob, ohp;
+                if (s <= 32) {
+                    sl = __shfl_sync(0xFFFFFFFFu, sl_l, j);
+                    oe = __shfl_sync(0xFFFFFFFFu, oe_l, j);
+                    ob = __shfl_sync(0xFFFFFFFFu, ob_l, j);
+                    ohp = __shfl_sync(0xFFFFFFFFu, ohp_l, j);
+                    if (!bit_of(sh.bits, sl)) continue;    // free, or its owner already evicted
+                } else {
+                    sl = slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp);
+                    if (!bit_of(sh.bits, sl)) continue;
+                    oe = owner[sl];
+                    ob = a.bstart[gb0 - a.bbase + (oe & kOwnerMask)];
+                    ohp = a.C * ((uint64_t)a.pilots[gb0 + (oe & kOwnerMask)] ^ a.seed);
+                }
                 const uint64_t os = oe >> kOwnerShift;
-                const uint64_t ob = a.bstart[gb0 - a.bbase + o];
-                const uint64_t ohp = a.C * ((uint64_t)a.pilots[gb0 + o] ^ a.seed);
                 for (uint64_t k = lane; k < os; k += 32) {
                     const uint32_t osl = slot_in_part<REDUCE>(a, a.sorted[ob + k] ^ ohp);
                     atomicAnd(&sh.bits[osl >> 5], ~(1u << (osl & 31)));
@@ -442,22 +477,46 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
 }
 
 // Greedy placement of small buckets (<= kSmallBucket keys) by every warp,
-// in deterministic rounds.  In a round each warp with a bucket finds its
-// smallest free pilot on the same snapshot of the bitvector; then a warp
-// commits its slots only if no earlier warp of the round picked any of
-// them (the others retry in the next round on the updated bitvector).
-// Buckets with no free pilot at all are placed by hash-evict (warp 0,
-// serially, with their cascade) before the next round.  Finished warps take
-// the next buckets of the stream in warp order, so the outcome depends only
-// on the input.
+// in deterministic rounds of kRoundCands candidates (kRoundQ per warp).  In
+// a round each candidate bucket finds its smallest free pilot on the same
+// snapshot of the bitvector; then a candidate commits its slots only if no
+// candidate of lower rank in the round picked any of them (the others
+// retry in the next round on the updated bitvector).  The comparison goes
+// through a claim table that keeps, per slot picked in the round, the
+// smallest rank that picked it.  Buckets with no free pilot at all are
+// placed by hash-evict (warp 0, serially, with their cascade) before the
+// next round.  Finished candidates take the next buckets of the stream in
+// rank order, so the outcome depends only on the input.
+constexpr int kRoundQ = 4;                              // candidates per warp
+constexpr int kRoundCands = kSearchWarps * kRoundQ;     // per round
+constexpr int kClaimSize = 1024;                        // >= 2 x kRoundCands x kSmallBucket
+
 struct RoundShared {
-    uint32_t slots[kSearchWarps][kSmallBucket];
-    int32_t chosen[kSearchWarps];     // pilot, -1: none found, -2: no bucket
-    uint32_t size[kSearchWarps];
-    uint32_t pos[kSearchWarps];       // stream position of the warp's bucket
-    uint32_t done[kSearchWarps];      // committed or deferred this round
+    uint32_t slots[kRoundCands][kSmallBucket];
+    int32_t chosen[kRoundCands];     // pilot, -1: none found, -2: no bucket
+    uint32_t size[kRoundCands];
+    uint32_t pos[kRoundCands];       // stream position of the candidate's bucket
+    uint32_t done[kRoundCands];      // committed or deferred this round
+    uint32_t claim_slot[kClaimSize]; // slot picked in this round, or kNone
+    uint32_t claim_rank[kClaimSize]; // smallest rank that picked it
     uint32_t cursor;
 };
+
+// Claim-table entry of slot sl (inserted when `insert`, else looked up; a
+// looked-up slot is always present).  The table is at most half full.
+__device__ __forceinline__ uint32_t claim_index(RoundShared &rs, uint32_t sl, bool insert) {
+    uint32_t idx = (sl * 2654435761u) >> 22;   // 10 bits: kClaimSize entries
+    for (int probe = 0; probe < kClaimSize; probe++) {
+        if (insert) {
+            const uint32_t prev = atomicCAS(&rs.claim_slot[idx], kNone, sl);
+            if (prev == kNone || prev == sl) return idx;
+        } else if (rs.claim_slot[idx] == sl) {
+            return idx;
+        }
+        idx = (idx + 1) & (kClaimSize - 1);
+    }
+    return idx;   // not reached: the table has free entries
+}
 
 template <int REDUCE>
 __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint64_t *order,
@@ -470,63 +529,87 @@ __device__ void greedy_rounds(const SearchArgs &a, const SearchShared &sh, Round
                               uint64_t p, int warp, int lane, unsigned long long &evicted, uint32_t *status) {
     const uint64_t gb0 = p * a.B;
     if (threadIdx.x == 0) {
-        for (int w = 0; w < kSearchWarps; w++) rs.pos[w] = first + w < last ? first + w : kNone;
-        rs.cursor = first + kSearchWarps < last ? first + kSearchWarps : last;
+        for (int c = 0; c < kRoundCands; c++) rs.pos[c] = first + c < last ? first + c : kNone;
+        rs.cursor = first + kRoundCands < last ? first + kRoundCands : last;
     }
+    for (int i = threadIdx.x; i < kClaimSize; i += blockDim.x) { rs.claim_slot[i] = kNone; rs.claim_rank[i] = kNone; }
     __syncthreads();
     for (;;) {
-        const uint32_t pos = rs.pos[warp];
-        uint32_t b = 0, z = 0;
-        int chosen = -2;
-        uint32_t my_sl = 0;
-        if (pos != kNone) {
-            const uint64_t d = order[pos];
-            b = (uint32_t)d;
-            z = (uint32_t)(d >> 32) & 0xFFFu;
-            const uint64_t myh = lane < (int)z ? ohash[(d >> 44) + lane] : 0;
-            chosen = greedy_small<REDUCE>(a, sh.bits, myh, (int)z, lane);
-            if (chosen >= 0 && lane < (int)z) {
-                my_sl = slot_in_part<REDUCE>(a, myh ^ (a.C * ((uint64_t)chosen ^ a.seed)));
-                rs.slots[warp][lane] = my_sl;
-            }
+        // 1. Search: the warp's candidates, their descriptors and hashes
+        //    requested together before any is searched.
+        uint64_t d[kRoundQ], myh[kRoundQ];
+#pragma unroll
+        for (int q = 0; q < kRoundQ; q++) {
+            const uint32_t pos = rs.pos[warp * kRoundQ + q];
+            d[q] = pos != kNone ? order[pos] : 0;
         }
-        if (lane == 0) { rs.chosen[warp] = chosen; rs.size[warp] = z; }
+#pragma unroll
+        for (int q = 0; q < kRoundQ; q++) {
+            const uint32_t z = (uint32_t)(d[q] >> 32) & 0xFFFu;
+            myh[q] = lane < (int)z ? ohash[(d[q] >> 44) + lane] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < kRoundQ; q++) {
+            const int c = warp * kRoundQ + q;
+            const uint32_t z = (uint32_t)(d[q] >> 32) & 0xFFFu;
+            int chosen = -2;
+            if (rs.pos[c] != kNone) {
+                chosen = greedy_small<REDUCE>(a, sh.bits, myh[q], (int)z, lane);
+                if (chosen >= 0 && lane < (int)z)
+                    rs.slots[c][lane] = slot_in_part<REDUCE>(a, myh[q] ^ (a.C * ((uint64_t)chosen ^ a.seed)));
+            }
+            if (lane == 0) { rs.chosen[c] = chosen; rs.size[c] = z; }
+        }
         __syncthreads();
-        // No warp has a bucket left: the phase is over.
+        // No candidate has a bucket left: the phase is over.
         bool any = false;
-        for (int w = 0; w < kSearchWarps; w++) any |= rs.chosen[w] != -2;
+        for (int c = 0; c < kRoundCands; c++) any |= rs.chosen[c] != -2;
         if (!any) break;
-        uint32_t done = 0;
-        if (chosen >= 0) {
-            bool clash = false;
-            if (lane < (int)z)
-                for (int w = 0; w < warp; w++) {
-                    if (rs.chosen[w] < 0) continue;
-                    for (uint32_t j = 0; j < rs.size[w]; j++) clash |= rs.slots[w][j] == my_sl;
-                }
-            if (!__any_sync(0xFFFFFFFFu, clash)) {
-                if (lane < (int)z) {
-                    atomicOr(&sh.bits[my_sl >> 5], 1u << (my_sl & 31));
-                    owner[my_sl] = pack_owner(b, z);
-                }
-                if (lane == 0) a.pilots[gb0 + b] = (uint8_t)chosen;
-                done = 1;
-            }
-        } else if (chosen == -1) {
-            done = 1;   // deferred below, in warp order
+        // 2. Claims: the smallest rank that picked each slot.
+#pragma unroll
+        for (int q = 0; q < kRoundQ; q++) {
+            const int c = warp * kRoundQ + q;
+            if (rs.chosen[c] >= 0 && lane < (int)rs.size[c])
+                atomicMin(&rs.claim_rank[claim_index(rs, rs.slots[c][lane], true)], (uint32_t)c);
         }
-        if (lane == 0) rs.done[warp] = done;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 0; w < kSearchWarps; w++) {
-                if (!rs.done[w]) continue;
-                if (rs.chosen[w] == -1) {
-                    const uint32_t i = (*sh.np)++;
-                    if (i < (uint32_t)kPendingCap) sh.pend[i] = pack_owner((uint32_t)order[rs.pos[w]], rs.size[w]);
+        // 3. Commit the candidates that own every slot they picked.
+#pragma unroll
+        for (int q = 0; q < kRoundQ; q++) {
+            const int c = warp * kRoundQ + q;
+            const int chosen = rs.chosen[c];
+            const uint32_t z = rs.size[c];
+            uint32_t done = 0;
+            if (chosen >= 0) {
+                const bool mine = lane >= (int)z || rs.claim_rank[claim_index(rs, rs.slots[c][lane], false)] == (uint32_t)c;
+                if (__all_sync(0xFFFFFFFFu, mine)) {
+                    const uint32_t b = (uint32_t)d[q];
+                    if (lane < (int)z) {
+                        const uint32_t sl = rs.slots[c][lane];
+                        atomicOr(&sh.bits[sl >> 5], 1u << (sl & 31));
+                        owner[sl] = pack_owner(b, z);
+                    }
+                    if (lane == 0) a.pilots[gb0 + b] = (uint8_t)chosen;
+                    done = 1;
                 }
-                rs.pos[w] = rs.cursor < last ? rs.cursor++ : kNone;
+            } else if (chosen == -1) {
+                done = 1;   // deferred below, in rank order
+            }
+            if (lane == 0) rs.done[c] = done;
+        }
+        __syncthreads();
+        // 4. Deferrals and refills in rank order; the claim table is emptied.
+        if (threadIdx.x == 0) {
+            for (int c = 0; c < kRoundCands; c++) {
+                if (!rs.done[c]) continue;
+                if (rs.chosen[c] == -1) {
+                    const uint32_t i = (*sh.np)++;
+                    if (i < (uint32_t)kPendingCap) sh.pend[i] = pack_owner((uint32_t)order[rs.pos[c]], rs.size[c]);
+                }
+                rs.pos[c] = rs.cursor < last ? rs.cursor++ : kNone;
             }
         }
+        for (int i = threadIdx.x; i < kClaimSize; i += blockDim.x) { rs.claim_slot[i] = kNone; rs.claim_rank[i] = kNone; }
         __syncthreads();
         // A bucket without a free pilot is placed now, by hash-evict, with
         // the whole cascade of evicted buckets, before the next round.
