@@ -257,6 +257,53 @@ __device__ __forceinline__ uint64_t bucket_size(const SearchArgs &a, uint64_t gb
     return a.bstart[gb0 - a.bbase + b + 1] - a.bstart[gb0 - a.bbase + b];
 }
 
+// Weighted-collision search of a small bucket (s <= MAXS keys, hashes in
+// lane j's myh): lane l scores pilot 32 r + l, CH chunks of 32 pilots at a
+// time so that the owner loads of CH chunks are in flight together.
+// Chunks are taken in increasing pilot order and a later chunk needs a
+// strictly lower cost, so ties go to the smaller pilot.
+template <int REDUCE, int MAXS, int CH>
+__device__ void evict_small(const SearchArgs &a, const SearchShared &sh, const uint32_t *owner, uint64_t myh, int s,
+                            int lane, bool use_tabu, uint64_t &best_cost, int &best_p) {
+    for (int r0 = 0; r0 < 8; r0 += CH) {
+        uint32_t sl[CH][MAXS], oe[CH][MAXS];
+        bool ok[CH];
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            const uint64_t hp = a.C * ((uint64_t)(32 * (r0 + c) + lane) ^ a.seed);
+            ok[c] = true;
+#pragma unroll
+            for (int j = 0; j < MAXS; j++) {
+                if (j >= s) break;
+                sl[c][j] = slot_in_part<REDUCE>(a, __shfl_sync(0xFFFFFFFFu, myh, j) ^ hp);
+                oe[c][j] = bit_of(sh.bits, sl[c][j]) ? owner[sl[c][j]] : kNone;
+#pragma unroll
+                for (int k = 0; k < j; k++) ok[c] &= sl[c][j] != sl[c][k];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            uint64_t cost = 0;
+#pragma unroll
+            for (int j = 0; j < MAXS; j++) {
+                if (j >= s) break;
+                if (oe[c][j] == kNone) continue;
+                if (use_tabu && in_recent(sh.recent, oe[c][j] & kOwnerMask)) ok[c] = false;
+                const uint64_t z = oe[c][j] >> kOwnerShift;
+                cost += z * z;
+            }
+            uint64_t cc = ok[c] ? cost : ~0ull;
+            int pp = ok[c] ? 32 * (r0 + c) + lane : 0x7FFFFFFF;
+            for (int off = 16; off; off >>= 1) {
+                const uint64_t oc = __shfl_xor_sync(0xFFFFFFFFu, cc, off);
+                const int op = __shfl_xor_sync(0xFFFFFFFFu, pp, off);
+                if (oc < cc || (oc == cc && op < pp)) { cc = oc; pp = op; }
+            }
+            if (cc < best_cost) { best_cost = cc; best_p = pp; }
+        }
+    }
+}
+
 // Least weighted collisions (Sec. 3.2): cost = sum over the bucket's keys
 // that hit a taken slot of size(owner)^2; pilots that self-collide or hit
 // one of the 16 most recently placed buckets are not allowed.  Ties go to
@@ -266,39 +313,12 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
                             uint64_t myh, int s, uint32_t &gen, int lane, bool use_tabu) {
     uint64_t best_cost = ~0ull;
     int best_p = -1;
+    if (s <= 4) {
+        evict_small<REDUCE, 4, 4>(a, sh, owner, myh, s, lane, use_tabu, best_cost, best_p);
+        return best_p;
+    }
     if (s <= kSmallBucket) {
-        for (int r = 0; r < 8; r++) {
-            const int p = 32 * r + lane;
-            const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
-            uint32_t sl[kSmallBucket], oe[kSmallBucket];
-            bool ok = true;
-            uint64_t cost = 0;
-            // Slots first and every owner load issued before any is used.
-#pragma unroll
-            for (int j = 0; j < kSmallBucket; j++) {
-                if (j >= s) break;
-                sl[j] = slot_in_part<REDUCE>(a, __shfl_sync(0xFFFFFFFFu, myh, j) ^ hp);
-                oe[j] = bit_of(sh.bits, sl[j]) ? owner[sl[j]] : kNone;
-#pragma unroll
-                for (int k = 0; k < j; k++) ok &= sl[j] != sl[k];
-            }
-#pragma unroll
-            for (int j = 0; j < kSmallBucket; j++) {
-                if (j >= s) break;
-                if (oe[j] == kNone) continue;
-                if (use_tabu && in_recent(sh.recent, oe[j] & kOwnerMask)) ok = false;
-                const uint64_t z = oe[j] >> kOwnerShift;
-                cost += z * z;
-            }
-            uint64_t c = ok ? cost : ~0ull;
-            int pp = ok ? p : 0x7FFFFFFF;
-            for (int off = 16; off; off >>= 1) {
-                const uint64_t oc = __shfl_xor_sync(0xFFFFFFFFu, c, off);
-                const int op = __shfl_xor_sync(0xFFFFFFFFu, pp, off);
-                if (oc < c || (oc == c && op < pp)) { c = oc; pp = op; }
-            }
-            if (c < best_cost) { best_cost = c; best_p = pp; }
-        }
+        evict_small<REDUCE, kSmallBucket, 1>(a, sh, owner, myh, s, lane, use_tabu, best_cost, best_p);
         return best_p;
     }
     for (int p = 0; p < 256; p++) {
@@ -489,7 +509,9 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
 // rank order, so the outcome depends only on the input.
 constexpr int kRoundQ = 4;                              // candidates per warp
 constexpr int kRoundCands = kSearchWarps * kRoundQ;     // per round
-constexpr int kClaimSize = 1024;                        // >= 2 x kRoundCands x kSmallBucket
+constexpr int kClaimBits = kRoundQ <= 4 ? 10 : 11;      // claim table of 2^kClaimBits entries,
+constexpr int kClaimSize = 1 << kClaimBits;             // at least twice the slots of a round
+static_assert(kClaimSize >= 2 * kRoundCands * kSmallBucket && kRoundCands % 32 == 0, "round shape");
 
 struct RoundShared {
     uint32_t slots[kRoundCands][kSmallBucket];
@@ -505,7 +527,7 @@ struct RoundShared {
 // Claim-table entry of slot sl (inserted when `insert`, else looked up; a
 // looked-up slot is always present).  The table is at most half full.
 __device__ __forceinline__ uint32_t claim_index(RoundShared &rs, uint32_t sl, bool insert) {
-    uint32_t idx = (sl * 2654435761u) >> 22;   // 10 bits: kClaimSize entries
+    uint32_t idx = (sl * 2654435761u) >> (32 - kClaimBits);
     for (int probe = 0; probe < kClaimSize; probe++) {
         if (insert) {
             const uint32_t prev = atomicCAS(&rs.claim_slot[idx], kNone, sl);
@@ -598,15 +620,30 @@ __device__ void greedy_rounds(const SearchArgs &a, const SearchShared &sh, Round
             if (lane == 0) rs.done[c] = done;
         }
         __syncthreads();
-        // 4. Deferrals and refills in rank order; the claim table is emptied.
-        if (threadIdx.x == 0) {
-            for (int c = 0; c < kRoundCands; c++) {
-                if (!rs.done[c]) continue;
-                if (rs.chosen[c] == -1) {
-                    const uint32_t i = (*sh.np)++;
+        // 4. Deferrals and refills in rank order (warp 0, 32 candidates per
+        //    step, ranks from ballots); the claim table is emptied.
+        if (warp == 0) {
+            for (int c0 = 0; c0 < kRoundCands; c0 += 32) {
+                const int c = c0 + lane;
+                const bool done = rs.done[c] != 0, deferred = done && rs.chosen[c] == -1;
+                const unsigned lt = (1u << lane) - 1;
+                const unsigned dm = __ballot_sync(0xFFFFFFFFu, done), fm = __ballot_sync(0xFFFFFFFFu, deferred);
+                const uint32_t np0 = *sh.np, cur0 = rs.cursor;
+                if (deferred) {
+                    const uint32_t i = np0 + __popc(fm & lt);
                     if (i < (uint32_t)kPendingCap) sh.pend[i] = pack_owner((uint32_t)order[rs.pos[c]], rs.size[c]);
                 }
-                rs.pos[c] = rs.cursor < last ? rs.cursor++ : kNone;
+                if (done) {
+                    const uint64_t nx = (uint64_t)cur0 + __popc(dm & lt);
+                    rs.pos[c] = nx < last ? (uint32_t)nx : kNone;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    *sh.np = np0 + __popc(fm);
+                    const uint64_t nc = (uint64_t)cur0 + __popc(dm);
+                    rs.cursor = nc < last ? (uint32_t)nc : last;
+                }
+                __syncwarp();
             }
         }
         for (int i = threadIdx.x; i < kClaimSize; i += blockDim.x) { rs.claim_slot[i] = kNone; rs.claim_rank[i] = kNone; }
