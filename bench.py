@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=float, default=1e9)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=1 << 26, help="oracle baseline sample (keys)")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 31,
+                    help="keys of the oracle baseline leg (2^31: about 13 s on 16 host cores)")
+    ap.add_argument("--ref-sample", type=int, default=1 << 26,
+                    help="keys per step of the reference arm (the oracle), so that K + W steps take seconds")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -556,7 +559,7 @@ def run_reference(args):
     keys = W.as_uint64_numpy(W.u64_keys(n, seed=0))
     ref = O.OracleMPHF.build_u64(keys, threads=cores)
     del keys
-    sample = min(int(args.cpu_sample), n)
+    sample = min(int(args.ref_sample), n)
     # A seeded sample of the query stream: keys of random indices.
     idx = W.uniform_index(sample, n, seed=1)
     qs = W.as_uint64_numpy(W.u64_keys_at(idx, seed=0))
