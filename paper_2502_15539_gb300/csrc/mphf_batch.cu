@@ -64,24 +64,27 @@ __device__ __forceinline__ uint32_t slot_any(const View &v, uint64_t h, uint64_t
 
 constexpr int kMaxReqSmem = 4096;   // request tile starts cached in shared memory
 
-// Persistent CTAs; tile t of request r covers keys [(t - first_tile[r]) * TK, ...).
+// Persistent CTAs whose warps take tiles on their own: tile t of request r
+// covers keys [(t - first_tile[r]) * 32 K, ...), lane l handling keys
+// l, l + 32, ... of it.  A warp asks for its next tile while it works on the
+// current one, so the atomic's latency is hidden, and no barrier ties the
+// warps of a block together after the request table is loaded.
 template <int K>
 __global__ void __launch_bounds__(512)
 batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restrict__ first_tile,
                    BatchHeader *__restrict__ hdr) {
     __shared__ uint32_t s_first[kMaxReqSmem + 1];
-    __shared__ uint32_t s_tile;
     extern __shared__ __align__(16) uint8_t s_stage[];   // kStrStage bytes per warp
     const uint32_t nreq = hdr->nreq, total = hdr->total_tiles;
     for (uint32_t i = threadIdx.x; i <= nreq && i <= kMaxReqSmem; i += blockDim.x) s_first[i] = first_tile[i];
     __syncthreads();
-    const uint32_t TK = blockDim.x * K;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&hdr->counter, 1u);
-        __syncthreads();
-        const uint32_t t = s_tile;
-        __syncthreads();
-        if (t >= total) break;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *stage = s_stage + (size_t)warp * kStrStage;
+    constexpr uint32_t TK = 32 * K;
+    uint32_t t = lane == 0 ? atomicAdd(&hdr->counter, 1u) : 0u;
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    while (t < total) {
+        const uint32_t tn = lane == 0 ? atomicAdd(&hdr->counter, 1u) : 0u;   // the next tile, in flight
         // The request owning tile t: the last r with first_tile[r] <= t.
         uint32_t lo = 0, hi = nreq;   // invariant: first[lo] <= t < first[hi]
         while (hi - lo > 1) {
@@ -92,6 +95,7 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
         const View v = d.v;
         const bool cubic = d.gamma == MPHF_GAMMA_CUBIC, pow2 = d.reduce == kReducePow2;
         const int remap = d.remap;
+        const uint32_t count = d.count;
         const uint64_t base = (uint64_t)(t - s_first[lo]) * TK;
         if (d.key_kind == MPHF_KEY_U64) {
             const uint64_t *keys = static_cast<const uint64_t *>(d.keys);
@@ -99,38 +103,36 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
             uint32_t p[K];
 #pragma unroll
             for (int q = 0; q < K; q++) {
-                const uint64_t i = base + (uint64_t)q * blockDim.x + threadIdx.x;
-                h[q] = v.C * (i < d.count ? __ldcs(keys + i) : 0ull);
+                const uint64_t i = base + 32u * q + lane;
+                h[q] = v.C * (i < count ? __ldcs(keys + i) : 0ull);
                 b[q] = bucket_any(v, h[q], part[q], cubic);
             }
 #pragma unroll
             for (int q = 0; q < K; q++) {
-                const uint64_t i = base + (uint64_t)q * blockDim.x + threadIdx.x;
-                p[q] = i < d.count ? __ldg(v.pilots + b[q]) : 0u;
+                const uint64_t i = base + 32u * q + lane;
+                p[q] = i < count ? __ldg(v.pilots + b[q]) : 0u;
             }
 #pragma unroll
             for (int q = 0; q < K; q++) {
-                const uint64_t i = base + (uint64_t)q * blockDim.x + threadIdx.x;
-                if (i < d.count) __stcs(d.out + i, slot_any(v, h[q], part[q], p[q], pow2, remap));
+                const uint64_t i = base + 32u * q + lane;
+                if (i < count) __stcs(d.out + i, slot_any(v, h[q], part[q], p[q], pow2, remap));
             }
         } else {
-            // Strings: each warp hashes groups of 32 consecutive strings of the
-            // tile through its shared-memory stage.
+            // Strings: groups of 32 consecutive strings through the warp's stage.
             const uint8_t *bytes = static_cast<const uint8_t *>(d.keys);
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-            uint8_t *stage = s_stage + (size_t)warp * kStrStage;
-            for (int g = warp; g < K * nwarps; g += nwarps) {
+            for (int g = 0; g < K; g++) {
                 const uint64_t w0 = base + 32ull * g;
-                if (w0 >= d.count) break;
-                const uint64_t hh = warp_hash_strings(bytes, d.offsets, w0, d.count, stage, v.seed, lane);
+                if (w0 >= count) break;
+                const uint64_t hh = warp_hash_strings(bytes, d.offsets, w0, count, stage, v.seed, lane);
                 const uint64_t i = w0 + lane;
-                if (i < d.count) {
+                if (i < count) {
                     uint64_t pt;
                     const uint64_t bb = bucket_any(v, hh, pt, cubic);
                     d.out[i] = slot_any(v, hh, pt, __ldg(v.pilots + bb), pow2, remap);
                 }
             }
         }
+        t = __shfl_sync(0xFFFFFFFFu, tn, 0);
     }
 }
 
@@ -232,7 +234,7 @@ static int stage_requests(mphf_batch *b, uint8_t *hb, const mphf_request *reqs, 
     BatchHeader *hdr = reinterpret_cast<BatchHeader *>(hb);
     uint32_t *first = reinterpret_cast<uint32_t *>(hb + off_first(b->cap));
     BatchDesc *desc = reinterpret_cast<BatchDesc *>(hb + off_desc(b->cap));
-    const uint64_t TK = (uint64_t)b->cfg.threads * b->cfg.keys_per_thread;
+    const uint64_t TK = 32ull * b->cfg.keys_per_thread;   // one warp's tile
     uint64_t tiles = 0;
     for (uint32_t i = 0; i < nreq; i++) {
         const mphf_request &r = reqs[i];
