@@ -111,8 +111,11 @@ typedef struct {
  *             Beyond 2^32 keys the values need the _wide queries, and the
  *             build runs in shards of whole parts (see shard_keys).
  * Runs on `stream` and returns once the structure is complete (it
- * synchronizes that stream).  Temporary device memory is allocated and freed
- * inside.  Errors: MPHF_ERR_ARG, MPHF_ERR_DUP_KEYS (equal u64 keys, or equal
+ * synchronizes that stream).  Temporary device memory comes from the
+ * stream-ordered allocator on `stream` and goes back to it, without
+ * synchronizing the device, so builds called from several host threads on
+ * different streams run concurrently (many small structures fill the GPU
+ * together).  Errors: MPHF_ERR_ARG, MPHF_ERR_DUP_KEYS (equal u64 keys, or equal
  * strings), MPHF_ERR_OVERFULL, MPHF_ERR_BUILD_FAILED, MPHF_ERR_OOM,
  * MPHF_ERR_CUDA.  On error *out is set to NULL. */
 int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,

@@ -19,6 +19,8 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "mphf_internal.cuh"
@@ -880,12 +882,76 @@ __global__ void narrow_kernel(const uint64_t *__restrict__ F, uint64_t len, uint
 }
 
 // ------------------------------------------------------------ orchestration
+// The builder's own stream-ordered memory pool, one per device.  It keeps
+// freed memory while any build runs (so concurrent and back-to-back builds
+// reuse it instead of mapping and unmapping pages at every synchronization)
+// and is trimmed when the last running build ends.
+struct BuildPool {
+    std::mutex mu;
+    cudaMemPool_t pool[64] = {};
+    int active[64] = {};
+};
+static BuildPool g_build_pool;
+
+static cudaError_t build_pool_enter(int dev, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lock(g_build_pool.mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_build_pool.pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&g_build_pool.pool[dev], &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(g_build_pool.pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+    }
+    g_build_pool.active[dev]++;
+    *out = g_build_pool.pool[dev];
+    return cudaSuccess;
+}
+
+// Called once the build's stream is idle (its last synchronization).
+static void build_pool_leave(int dev) {
+    std::lock_guard<std::mutex> lock(g_build_pool.mu);
+    if (--g_build_pool.active[dev] == 0) cudaMemPoolTrimTo(g_build_pool.pool[dev], 0);
+}
+
+struct PoolGuard {   // leaves the pool on every return path, after its buffers
+    int dev = -1;
+    cudaStream_t s = nullptr;
+    ~PoolGuard() {
+        if (dev < 0) return;
+        cudaStreamSynchronize(s);
+        build_pool_leave(dev);
+    }
+};
+
+// Device memory of one build, taken from and returned to the pool on the
+// build's stream: neither step synchronizes the device, so builds on
+// different streams (from different host threads) overlap.
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    cudaStream_t s = nullptr;
+    cudaMemPool_t pool = nullptr;
+    DevBuf(cudaStream_t st, cudaMemPool_t pl) : s(st), pool(pl) {}
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { if (p) cudaFreeAsync(p, s); }
     template <class T> T *as() const { return static_cast<T *>(p); }
-    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+    cudaError_t alloc(size_t bytes) {   // pool NULL: the device's default pool
+        return pool ? cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool, s) : cudaMallocAsync(&p, bytes ? bytes : 16, s);
+    }
     void *release() { void *q = p; p = nullptr; return q; }
+};
+
+struct EventPair {   // timing events of a build, destroyed on every return path
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    ~EventPair() {
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+    }
 };
 
 // Dynamic shared memory of pilot_search_kernel for S slots per part.
@@ -901,10 +967,22 @@ static unsigned grid_for(uint64_t work, int sms) {
     return (unsigned)(want == 0 ? 1 : (want < cap ? want : cap));
 }
 
+// The dynamic shared-memory limit of the search kernel is raised once per
+// device, to what the largest part (S = kMaxSlots) needs, so that builds of
+// different S running from several threads never lower it under each other.
 template <int REDUCE>
 static cudaError_t launch_search(const SearchArgs &a, unsigned grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(pilot_search_kernel<REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<uint64_t> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(opted.load() & bit)) {
+        e = cudaFuncSetAttribute(pilot_search_kernel<REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)search_smem_bytes(kMaxSlots));
+        if (e != cudaSuccess) return e;
+        opted.fetch_or(bit);
+    }
     pilot_search_kernel<REDUCE><<<grid, kSearchThreads, smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
@@ -925,10 +1003,10 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
 
-    cudaEvent_t t0, t1;
-    CK(cudaEventCreate(&t0));
-    CK(cudaEventCreate(&t1));
-    CK(cudaEventRecord(t0, s));
+    EventPair ev;
+    CK(cudaEventCreate(&ev.t0));
+    CK(cudaEventCreate(&ev.t1));
+    CK(cudaEventRecord(ev.t0, s));
 
     const uint64_t total = P * S, nbkt = P * B, words = (total + 31) / 32;
     // Shards of whole parts (the in-memory sharding of Appendix B): every
@@ -955,7 +1033,15 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     // (Sec. 3.1): its high half picks part and bucket, its low half the slot,
     // and the keys are sorted by (high, low) with two stable radix passes.
     const bool h128 = key_kind == MPHF_KEY_BYTES && (prm.hash128 != 0 || n > (1ull << 32));
-    DevBuf hash, sorted, hash_hi, sorted_hi, bstart, pilots, taken, owner, order, ohash, status, flags, cub_tmp;
+    PoolGuard guard;
+    cudaMemPool_t pool = nullptr;
+    CK(build_pool_enter(dev, &pool));
+    guard.dev = dev;
+    guard.s = s;
+    DevBuf hash(s, pool), sorted(s, pool), hash_hi(s, pool), sorted_hi(s, pool), bstart(s, pool), taken(s, pool),
+        owner(s, pool), order(s, pool), ohash(s, pool), status(s, pool), flags(s, pool), cub_tmp(s, pool);
+    // The structure's own arrays outlive the build: the default allocator.
+    DevBuf pilots(s, nullptr);
     CK(hash.alloc(cap * 8));
     CK(sorted.alloc(cap * 8));
     if (h128) {
@@ -1098,7 +1184,8 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
 
     // Remap (Sec. 3.4).
     const uint64_t len = total - n;
-    DevBuf free_cnt, high_cnt, free_rank, high_rank, L, F, remap;
+    DevBuf free_cnt(s, pool), high_cnt(s, pool), free_rank(s, pool), high_rank(s, pool), L(s, pool), F(s, nullptr),
+        remap(s, nullptr);
     CK(free_cnt.alloc(words * 4));
     CK(high_cnt.alloc(words * 4));
     CK(free_rank.alloc((words + 1) * 4));
@@ -1108,7 +1195,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     count_launch();
     size_t scan_tmp = 0;
     CK(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, free_cnt.as<uint32_t>(), free_rank.as<uint32_t>(), words, s));
-    DevBuf scan_buf;
+    DevBuf scan_buf(s, pool);
     CK(scan_buf.alloc(scan_tmp));
     CK(cub::DeviceScan::ExclusiveSum(scan_buf.p, scan_tmp, free_cnt.as<uint32_t>(), free_rank.as<uint32_t>(), words, s));
     CK(cub::DeviceScan::ExclusiveSum(scan_buf.p, scan_tmp, high_cnt.as<uint32_t>(), high_rank.as<uint32_t>(), words, s));
@@ -1141,7 +1228,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
         CK(cudaMemcpyAsync(&span_fail, d_flags + 3, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (span_fail) {               // a line's values span too far: plain array instead
-            cudaFree(remap.release());
+            cudaFreeAsync(remap.release(), s);
             remap_kind = MPHF_REMAP_VEC;
         } else {
             h.remap_bytes = lines * 64;
@@ -1162,12 +1249,10 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     }
     h.remap = remap_kind;
     CK(cudaGetLastError());
-    CK(cudaEventRecord(t1, s));
-    CK(cudaEventSynchronize(t1));
+    CK(cudaEventRecord(ev.t1, s));
+    CK(cudaEventSynchronize(ev.t1));
     float ms = 0;
-    cudaEventElapsedTime(&ms, t0, t1);
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
+    cudaEventElapsedTime(&ms, ev.t0, ev.t1);
     out->hdr = h;
     out->d_pilots = static_cast<uint8_t *>(pilots.release());
     out->d_remap = static_cast<uint8_t *>(remap.p ? remap.release() : nullptr);

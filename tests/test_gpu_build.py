@@ -161,3 +161,29 @@ def test_gpu_build_128_bit_duplicate_strings_rejected():
     with pytest.raises(N.MphfError) as e:
         N.mphf_build(data.cuda(), N.mphf_default_params(max_reseeds=2, hash128=1), offsets=off.cuda())
     assert e.value.code == N.MPHF_ERR_DUP_KEYS
+
+
+def test_concurrent_builds_from_threads_match_sequential_builds():
+    """Builds from several host threads, each on its own stream, overlap on
+    the GPU (stream-ordered temporaries, one fixed shared-memory limit) and
+    give the same bytes as one build at a time."""
+    from concurrent.futures import ThreadPoolExecutor
+    N = need_gpu()
+    ns = [1000, 50_000, 300_000, 2_000_000, 7_000, 900_000, 120_000, 4_000_000]
+    keys = [W.u64_keys(n, 40 + i).cuda() for i, n in enumerate(ns)]
+    data, off = W.strings(torch.arange(200_000), seed=41)
+    data, off = data.cuda(), off.cuda()
+    want = [N.mphf_serialize(N.mphf_build(k)) for k in keys] + [N.mphf_serialize(N.mphf_build(data, offsets=off))]
+
+    def build(i):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            if i < len(keys):
+                m = N.mphf_build(keys[i], stream=stream)
+            else:
+                m = N.mphf_build(data, offsets=off, stream=stream)
+        return N.mphf_serialize(m)
+
+    with ThreadPoolExecutor(max_workers=len(want)) as pool:
+        got = list(pool.map(build, range(len(want))))
+    assert got == want
