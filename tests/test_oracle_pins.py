@@ -459,21 +459,22 @@ def test_string_hash128_high_half_is_uniform():
     assert float(((counts - exp) ** 2 / exp).sum()) < 45   # 15 dof; p ~ 1e-4
 
 
-@pytest.mark.parametrize("n", [1, 300, 20_000])
-def test_string_build_with_128_bit_hash(n):
+@pytest.mark.parametrize("n,params", [(1, {}), (300, {}), (20_000, {}),
+                                      (30_000, {"slots_override": 2048, "alpha": 0.9})])   # 17 parts
+def test_string_build_with_128_bit_hash(n, params):
     """Byte keys with the 128-bit hash (forced here; automatic past 2^32
     keys): the high half picks part and bucket, the low half the slot; the
     result is still a bijection, and the flag survives serialization."""
     data, off = W.strings(torch.arange(n), seed=8)
     d, o = data.numpy(), off.numpy().astype(np.uint64)
-    m = O.OracleMPHF.build_bytes(d, o, hash128=1)
+    m = O.OracleMPHF.build_bytes(d, o, hash128=1, **params)
     got = m.query_bytes(d, o)
     assert sorted(got.tolist()) == list(range(n))
     blob = m.serialize()
     assert int.from_bytes(blob[28:32], "little") == 1
     m2 = O.OracleMPHF.deserialize(blob)
     assert np.array_equal(m2.query_bytes(d, o), got)
-    plain = O.OracleMPHF.build_bytes(d, o)
+    plain = O.OracleMPHF.build_bytes(d, o, **params)
     assert int.from_bytes(plain.serialize()[28:32], "little") == 0
 
 
@@ -481,11 +482,12 @@ def test_128_bit_hash_places_keys_by_the_high_half():
     """For a key of a 128-bit structure, its slot follows Eq. partbucket on
     the high half and Eq. slot on the low half: the slot read from the
     structure's own pilot matches, and the part is hi(P * high)."""
-    n = 5000
+    n = 30_000
     data, off = W.strings(torch.arange(n), seed=9)
     d, o = data.numpy(), off.numpy().astype(np.uint64)
-    m = O.OracleMPHF.build_bytes(d, o, hash128=1)
+    m = O.OracleMPHF.build_bytes(d, o, hash128=1, slots_override=2048, alpha=0.9)   # 17 parts
     L = m.layout
+    assert L.P > 1
     for i in range(0, n, 97):
         hi, lo = O.hash_bytes128(d[o[i]:o[i + 1]].tobytes(), m.seed)
         s = O.lib().orc_slot_of_hash2(m._h, hi, lo)
