@@ -239,7 +239,8 @@ def test_gather_probe_reads_the_table():
 
 
 @pytest.mark.parametrize("n,params", [(37, {}), (5000, {}), (100_000, {}),
-                                      (60_000, {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC})])
+                                      (60_000, {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC}),
+                                      (30_000, {"slots_override": 2048, "alpha": 0.9})])   # 17 parts
 def test_query_bytes_128_bit_hash_matches_oracle(n, params):
     """Structures whose strings use the 128-bit hash (high half: part and
     bucket; low half: slot; Sec. 3.1), built by the oracle: the 32- and
