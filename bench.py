@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-strings", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the PHF / Fast / Compact leg")
+    ap.add_argument("--no-wide", action="store_true", help="skip the leg past 2^32 keys")
+    ap.add_argument("--wide-n", type=float, default=4.5e9, help="keys of the leg past 2^32 keys")
     ap.add_argument("--strings-n", type=float, default=3e8)
     ap.add_argument("--serve-requests", type=int, default=800)
     ap.add_argument("--batch-mphfs", type=int, default=256)
@@ -267,7 +270,10 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, q, args.cpu_sample)
-    del q, out
+    variants = None if args.no_variants else run_variants(args, m, q, out, stream, time_steps)
+    del q, out, m
+    torch.cuda.empty_cache()
+    wide = None if args.no_wide else run_wide(args, dev, stream)
     torch.cuda.empty_cache()
     batched = None if args.no_batched else run_batched(args, dev, stream)
     torch.cuda.empty_cache()
@@ -303,6 +309,8 @@ def run_gpu(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "variants": variants,
+            "wide": wide,
             "batched": batched,
             "strings": strings,
             "serving": serving,
@@ -310,6 +318,70 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_variants(args, m, q, out, stream, time_steps):
+    """The other parameter sets of Table remap on the same keys and query
+    stream: the PHF query of the Default structure (slots, no remap), Fast
+    (gamma_1, lambda 3.0, plain remap array) and Compact (lambda 4.0), each
+    built on the GPU and timed like the main leg."""
+    from paper_2502_15539_gb300 import native as N
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        return statistics.mean(time_steps(fn, args.steps))
+
+    mq = q.numel()
+    ms = timed(lambda: N.mphf_query_u64_phf(m, q, out, stream=stream))
+    res = {"default_phf": {"query_ms": ms, "queries_per_s": mq / (ms / 1e3)}}
+    for name, prm in (("fast", {"lam": 3.0, "gamma": 1, "remap": 1}), ("compact", {"lam": 4.0})):
+        mv = N.mphf_build(q, N.mphf_default_params(**prm))
+        info = N.mphf_info(mv)
+        ms = timed(lambda: N.mphf_query_u64(mv, q, out, stream=stream))
+        res[name] = {"params": prm, "query_ms": ms, "queries_per_s": mq / (ms / 1e3),
+                     "bits_per_key": info["bits_per_key"], "build_ms": info["build_ms"]}
+        del mv
+    return res
+
+
+def run_wide(args, dev, stream):
+    """Past 2^32 keys: wide_n distinct u64 keys, built on the GPU in shards of
+    whole parts, queried in key order with 64-bit results.  The results are
+    checked to be a bijection onto [0, n) on the device."""
+    import torch
+    from paper_2502_15539_gb300 import native as N
+    from paper_2502_15539_gb300 import workloads as W
+
+    n = int(args.wide_n)
+    chunk = 1 << 28
+    keys = torch.empty(n, dtype=torch.int64, device=dev)
+    for s0 in range(0, n, chunk):
+        keys[s0:s0 + chunk] = W.u64_keys(min(chunk, n - s0), seed=3, device=dev, start=s0)
+    m = N.mphf_build(keys)
+    info = N.mphf_info(m)
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    N.mphf_query_u64_wide(m, keys, out, stream=stream)   # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 3))
+    a.record(stream)
+    for _ in range(steps):
+        N.mphf_query_u64_wide(m, keys, out, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    del keys
+    bijective = False
+    if int(out.min().item()) >= 0 and int(out.max().item()) < n:   # in range: the fill stays in bounds
+        seen = torch.zeros(n, dtype=torch.uint8, device=dev)
+        seen.index_fill_(0, out, 1)
+        bijective = int(seen.sum(dtype=torch.int64).item()) == n
+        del seen
+    del out, m
+    return {"workload": f"{n} distinct u64 keys (> 2^32), query all in key order, 64-bit results",
+            "P": info["P"], "S": info["S"], "bits_per_key": info["bits_per_key"],
+            "build_ms": info["build_ms"], "build_ns_per_key": 1e6 * info["build_ms"] / n,
+            "query_ms": ms, "queries_per_s": n / (ms / 1e3), "output_bijective": bijective}
 
 
 def run_batched(args, dev, stream):
