@@ -76,7 +76,7 @@ query_u64_wide_kernel(const View v, const uint64_t *__restrict__ keys, const uin
 
 // VEC: keys 16-byte and out 8-byte aligned; pairs of keys per load / store.
 template <int GAMMA, int REDUCE, int REMAP, bool PHF, bool VEC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 query_u64_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
                  uint32_t *__restrict__ out) {
     constexpr int K = kKeysPerThread;
