@@ -69,8 +69,10 @@ constexpr int kMaxReqSmem = 4096;   // request tile starts cached in shared memo
 // l, l + 32, ... of it.  A warp asks for its next tile while it works on the
 // current one, so the atomic's latency is hidden, and no barrier ties the
 // warps of a block together after the request table is loaded.
+// Up to 4 keys per lane the registers allow 1536 resident threads per SM
+// (more warps to hide the latency of each tile); 8 and 16 keys need more.
 template <int K>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, K <= 4 ? 3 : (K == 8 ? 2 : 1))
 batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restrict__ first_tile,
                    BatchHeader *__restrict__ hdr) {
     __shared__ uint32_t s_first[kMaxReqSmem + 1];
