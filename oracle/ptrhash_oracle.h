@@ -102,7 +102,8 @@ uint64_t orc_hash_u64(uint64_t C, uint64_t k);
 uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed);
 /* The 128-bit variant: *lo is orc_hash_bytes, *hi the same construction
  * with its own seed tweak and fold constant.  hi picks the part and bucket,
- * lo the slot. */
+ * lo the slot.  Parity unpinned against external values, like the 64-bit
+ * hash; pinned by structural properties in the tests. */
 void     orc_hash_bytes128(const uint8_t *s, uint64_t len, uint64_t seed, uint64_t *hi, uint64_t *lo);
 uint64_t orc_hp(uint64_t C, uint64_t seed, uint64_t pilot);
 uint64_t orc_reduce(int reduce, uint64_t C, uint64_t x, uint64_t S);
