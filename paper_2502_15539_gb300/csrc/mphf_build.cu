@@ -255,10 +255,6 @@ __device__ int greedy_large(const SearchArgs &a, const SearchShared &sh, int s, 
     return -1;
 }
 
-__device__ __forceinline__ uint64_t bucket_size(const SearchArgs &a, uint64_t gb0, uint32_t b) {
-    return a.bstart[gb0 - a.bbase + b + 1] - a.bstart[gb0 - a.bbase + b];
-}
-
 // Weighted-collision search of a small bucket (s <= MAXS keys, hashes in
 // lane j's myh): lane l scores pilot 32 r + l, CH chunks of 32 pilots at a
 // time so that the owner loads of CH chunks are in flight together.
