@@ -1,9 +1,11 @@
 // GPU construction of a PtrHash structure (Sec. 3.2 and Sec. 3.4).
 //
-//   1. hash every key                                   (hash_keys_kernel)
-//   2. radix-sort the 64-bit hashes (CUB); sorted hashes are grouped by part
-//      and, inside a part, by bucket, because part = hi(P h) and the bucket
-//      function are monotone in h
+//   1. hash every key (hash_keys_kernel), or, in shards of whole parts, the
+//      keys of one shard's parts (shard_hash_kernel); byte keys past 2^32
+//      keys take the 128-bit hash, whose high half picks part and bucket
+//   2. radix-sort the 64-bit hashes (CUB; 128-bit ones by (high, low));
+//      sorted hashes are grouped by part and, inside a part, by bucket,
+//      because part = hi(P h) and the bucket function are monotone in h
 //   3. bucket boundaries, duplicate and part-size checks  (bucket_bounds_kernel)
 //   4. pilot search, one CTA per part, the part's taken-slot bitvector in
 //      shared memory: buckets in order of decreasing size, the smallest pilot
@@ -14,7 +16,8 @@
 //      evict_mult * S evictions                              (pilot_search_kernel)
 //   5. remap: the R taken slots >= n in order go to the R free slots < n in
 //      order, F[q - n]; other entries repeat their predecessor; CacheLineEF
-//      encoding of F, or a plain u32 array if a line's span does not fit.
+//      encoding of F, or a plain array (u32, u64 past 2^32 keys) if a line's
+//      span does not fit.
 // A failed part or equal string hashes restart from step 1 with seed + 1.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
