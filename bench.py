@@ -302,7 +302,10 @@ def run_gpu(args):
                          "kernel": "query_u64_kernel"},
             "gather_roofline": {"probe_ms": probe_ms, "query_ms": kernel_ms, "frac": probe_ms / kernel_ms,
                                 "probe": "mphf_gather_probe: same key stream, 1 random byte of a "
-                                         f"{info['pilot_bytes']}-byte table per key"},
+                                         f"{info['pilot_bytes']}-byte table per key",
+                                "pilot_gathers_per_s": mq / (kernel_ms / 1e3),
+                                "key_stream_gbs": 8 * mq / (kernel_ms / 1e3) / 1e9,
+                                "result_stream_gbs": 4 * mq / (kernel_ms / 1e3) / 1e9},
             "remapped_fraction": remapped / mq,
             "build": {"ms": info["build_ms"], "ns_per_key": 1e6 * info["build_ms"] / n,
                       "evictions": info["evictions"]},
