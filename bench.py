@@ -308,7 +308,8 @@ def run_gpu(args):
                                 "result_stream_gbs": 4 * mq / (kernel_ms / 1e3) / 1e9},
             "remapped_fraction": remapped / mq,
             "build": {"ms": info["build_ms"], "ns_per_key": 1e6 * info["build_ms"] / n,
-                      "evictions": info["evictions"]},
+                      "evictions": info["evictions"], "hash_sort_ms": info["build_hash_sort_ms"],
+                      "search_ms": info["build_search_ms"], "remap_ms": info["build_remap_ms"]},
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -97,6 +97,9 @@ typedef struct {
     double   bits_per_key;    /* 8 (pilot_bytes + remap_bytes) / n              */
     uint64_t evictions;       /* hash-evict evictions of the build (0 if loaded)*/
     double   build_ms;        /* device time of mphf_build (0 if loaded)        */
+    double   build_hash_sort_ms;  /* of which hashing, sorting, bucket bounds   */
+    double   build_search_ms;     /* pilot search (Sec. 3.2)                    */
+    double   build_remap_ms;      /* remap and CacheLineEF encoding (Sec. 3.4)  */
 } mphf_info_t;
 
 /* --------------------------------------------------------------- build */

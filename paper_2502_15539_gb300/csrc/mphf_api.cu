@@ -16,6 +16,7 @@ struct mphf {
     int device = 0;
     uint64_t evictions = 0;
     double build_ms = 0.0;
+    double hash_sort_ms = 0.0, search_ms = 0.0, remap_ms = 0.0;
     // Staging for mphf_query_u64_host: two buffer sets, two copy streams.
     std::mutex stage_mu;
     uint64_t stage_chunk = 0;
@@ -367,6 +368,9 @@ int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
     m->d_remap = r.d_remap;
     m->evictions = r.evictions;
     m->build_ms = r.build_ms;
+    m->hash_sort_ms = r.hash_sort_ms;
+    m->search_ms = r.search_ms;
+    m->remap_ms = r.remap_ms;
     cudaGetDevice(&m->device);
     *out = m;
     return MPHF_OK;
@@ -384,6 +388,9 @@ int mphf_info(const mphf_t *m, mphf_info_t *out) {
     out->bits_per_key = 8.0 * (double)(out->pilot_bytes + out->remap_bytes) / (double)h.n;
     out->evictions = m->evictions;
     out->build_ms = m->build_ms;
+    out->build_hash_sort_ms = m->hash_sort_ms;
+    out->build_search_ms = m->search_ms;
+    out->build_remap_ms = m->remap_ms;
     return MPHF_OK;
 }
 

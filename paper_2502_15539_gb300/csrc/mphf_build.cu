@@ -946,10 +946,16 @@ struct DevBuf {
 };
 
 struct EventPair {   // timing events of a build, destroyed on every return path
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;   // the whole build
+    cudaEvent_t a = nullptr, b = nullptr;     // one phase
     ~EventPair() {
-        if (t0) cudaEventDestroy(t0);
-        if (t1) cudaEventDestroy(t1);
+        for (cudaEvent_t e : {t0, t1, a, b})
+            if (e) cudaEventDestroy(e);
+    }
+    // Milliseconds between a and b, once b has completed.
+    double phase_ms() const {
+        float ms = 0;
+        return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.0;
     }
 };
 
@@ -1005,7 +1011,10 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     EventPair ev;
     CK(cudaEventCreate(&ev.t0));
     CK(cudaEventCreate(&ev.t1));
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
     CK(cudaEventRecord(ev.t0, s));
+    double hash_sort_ms = 0, search_ms = 0;
 
     const uint64_t total = P * S, nbkt = P * B, words = (total + 31) / 32;
     // Shards of whole parts (the in-memory sharding of Appendix B): every
@@ -1082,6 +1091,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
         bool ok = true;
         for (uint64_t sh = 0; sh < shards && ok; sh++) {
             const uint64_t p_lo = P * sh / shards, p_hi = P * (sh + 1) / shards;
+            CK(cudaEventRecord(ev.a, s));
             CK(cudaMemsetAsync(d_flags, 0, 64, s));
             uint64_t m = n;
             if (shards == 1) {
@@ -1129,8 +1139,10 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
                 part_size_kernel<<<grid_for(p_hi - p_lo, sms), 256, 0, s>>>(bstart.as<uint32_t>(), p_hi - p_lo, B, S, d_flags + 1);
                 count_launch(2);
                 CK(cudaGetLastError());
+                CK(cudaEventRecord(ev.b, s));
                 CK(cudaMemcpyAsync(hf, d_flags, 8, cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
+                hash_sort_ms += ev.phase_ms();
             } else {
                 hf[1] = 1;
             }
@@ -1160,14 +1172,17 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
             a.evict_cap = (uint64_t)prm.evict_mult * S;
             a.part_begin = p_lo; a.part_end = p_hi; a.bbase = p_lo * B;
             const unsigned grid = (unsigned)(p_hi - p_lo < (uint64_t)search_grid ? p_hi - p_lo : (uint64_t)search_grid);
+            CK(cudaEventRecord(ev.a, s));
             CK(reduce == kReducePow2 ? launch_search<kReducePow2>(a, grid, smem, s)
                                      : launch_search<kReduceMod>(a, grid, smem, s));
+            CK(cudaEventRecord(ev.b, s));
             std::vector<uint32_t> st(p_hi - p_lo);
-            unsigned long long ev = 0;
+            unsigned long long nev = 0;
             CK(cudaMemcpyAsync(st.data(), status.as<uint32_t>() + p_lo, (p_hi - p_lo) * 4, cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(&ev, d_flags + 4, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&nev, d_flags + 4, 8, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            evictions_total += ev;
+            search_ms += ev.phase_ms();
+            evictions_total += nev;
             uint64_t failed = 0, first_bad = 0;
             for (uint64_t q = 0; q < p_hi - p_lo; q++) if (st[q] != kPartOk) { if (!failed) first_bad = p_lo + q; failed++; }
             if (failed) {
@@ -1182,6 +1197,7 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     if (!built) return last_fail;
 
     // Remap (Sec. 3.4).
+    CK(cudaEventRecord(ev.a, s));
     const uint64_t len = total - n;
     DevBuf free_cnt(s, pool), high_cnt(s, pool), free_rank(s, pool), high_rank(s, pool), L(s, pool), F(s, nullptr),
         remap(s, nullptr);
@@ -1250,8 +1266,9 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     CK(cudaGetLastError());
     CK(cudaEventRecord(ev.t1, s));
     CK(cudaEventSynchronize(ev.t1));
-    float ms = 0;
+    float ms = 0, remap_ms = 0;
     cudaEventElapsedTime(&ms, ev.t0, ev.t1);
+    cudaEventElapsedTime(&remap_ms, ev.a, ev.t1);
     out->hdr = h;
     out->d_pilots = static_cast<uint8_t *>(pilots.release());
     out->d_remap = static_cast<uint8_t *>(remap.p ? remap.release() : nullptr);
@@ -1261,6 +1278,9 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
     }
     out->evictions = evictions_total;
     out->build_ms = ms;
+    out->hash_sort_ms = hash_sort_ms;
+    out->search_ms = search_ms;
+    out->remap_ms = remap_ms;
     return MPHF_OK;
 }
 

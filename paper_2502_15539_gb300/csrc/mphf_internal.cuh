@@ -81,6 +81,7 @@ struct BuildResult {
     uint8_t *d_remap = nullptr;
     uint64_t evictions = 0;
     double build_ms = 0.0;
+    double hash_sort_ms = 0.0, search_ms = 0.0, remap_ms = 0.0;   // phases, summed over shards and seeds
 };
 int build_structure(const mphf_params &p, int key_kind, const void *keys, const uint64_t *offsets,
                     uint64_t n, cudaStream_t s, BuildResult *out);

@@ -58,7 +58,8 @@ class mphf_info_t(ctypes.Structure):
                 ("key_kind", ctypes.c_int32), ("remap_len", ctypes.c_uint64),
                 ("pilot_bytes", ctypes.c_uint64), ("remap_bytes", ctypes.c_uint64),
                 ("bits_per_key", ctypes.c_double), ("evictions", ctypes.c_uint64),
-                ("build_ms", ctypes.c_double)]
+                ("build_ms", ctypes.c_double), ("build_hash_sort_ms", ctypes.c_double),
+                ("build_search_ms", ctypes.c_double), ("build_remap_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

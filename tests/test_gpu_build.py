@@ -187,3 +187,16 @@ def test_concurrent_builds_from_threads_match_sequential_builds():
     with ThreadPoolExecutor(max_workers=len(want)) as pool:
         got = list(pool.map(build, range(len(want))))
     assert got == want
+
+
+def test_build_reports_its_phase_times():
+    """mphf_info splits the device time of a build into hashing and sorting,
+    the pilot search and the remap; the three fit inside the whole."""
+    N = need_gpu()
+    m = N.mphf_build(W.u64_keys(2_000_000, 11).cuda())
+    info = N.mphf_info(m)
+    phases = (info["build_hash_sort_ms"], info["build_search_ms"], info["build_remap_ms"])
+    assert all(t > 0 for t in phases)
+    assert sum(phases) <= info["build_ms"] * 1.001
+    loaded = N.mphf_info(N.mphf_deserialize(N.mphf_serialize(m)))
+    assert loaded["build_ms"] == 0 and loaded["build_search_ms"] == 0
