@@ -161,6 +161,7 @@ struct SearchShared {
     uint32_t *pend;     // kPendingCap waiting buckets (bucket | size << 20)
     uint32_t *np;       // how many
     uint32_t *recent;   // 16
+    struct CoopReq *coop;   // block-cooperative pilot scoring (see below)
 };
 
 constexpr int kSearchWarps = kSearchThreads / 32;
@@ -344,15 +345,204 @@ __device__ int evict_choice(const SearchArgs &a, const SearchShared &sh, const u
     return best_p;
 }
 
+// ------------------------------------------- block-cooperative pilot scoring
+// During the eviction drains between rounds, warp 0 places buckets one by
+// one while the other warps would wait at a barrier.  Instead they score
+// pilots for it: warp 0 posts a request (the bucket's hashes and what to
+// compute) and warp w takes pilots 32 w .. 32 w + 31, so all 256 pilots of
+// a greedy search or of a weighted-collision search are tried in one step.
+// Warp 0 and the helpers meet at two named barriers per request (all
+// threads of the block take part in both).  Warp 0 ends every drain with a
+// kCoopDone request, on every return path, which releases the helpers.
+// The results are those of greedy_small and evict_small: chunks are taken
+// in pilot order and ties go to the smaller pilot.
+enum : int { kCoopGreedy = 0, kCoopEvictTabu = 1, kCoopEvict = 2, kCoopLarge = 3, kCoopDone = 4 };
+struct CoopReq {
+    uint64_t h[kSmallBucket];                  // the bucket's hashes (large buckets: sh.hcache)
+    int32_t s, kind;
+    unsigned long long cost[kSearchWarps];     // per warp: best cost of its chunk
+    int32_t pilot[kSearchWarps];               // per warp: best pilot of its chunk, or -1
+    uint32_t mask[kSearchWarps];               // per warp: large-bucket pilots on free slots
+};
+
+// Barrier `id` (1 or 2; 0 is __syncthreads) of all kSearchThreads threads,
+// entered by a converged warp.
+__device__ __forceinline__ void named_barrier(int id) {
+    __syncwarp();
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(kSearchThreads) : "memory");
+}
+
+// The smallest pilot of chunk w whose keys land on distinct free slots, or -1.
+template <int REDUCE>
+__device__ int coop_greedy_share(const SearchArgs &a, const uint32_t *bits, const CoopReq &q, int w, int lane) {
+    const int s = q.s;
+    const uint64_t hp = a.C * ((uint64_t)(32 * w + lane) ^ a.seed);
+    uint32_t sl[kSmallBucket];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < kSmallBucket; j++) {
+        if (j >= s) break;
+        sl[j] = slot_in_part<REDUCE>(a, q.h[j] ^ hp);
+        ok &= !bit_of(bits, sl[j]);
+#pragma unroll
+        for (int k = 0; k < j; k++) ok &= sl[j] != sl[k];
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+    return m ? 32 * w + __ffs(m) - 1 : -1;
+}
+
+// The least weighted-collision pilot of chunk w (cost ~0 if none allowed).
+template <int REDUCE>
+__device__ void coop_evict_share(const SearchArgs &a, const SearchShared &sh, const uint32_t *owner, const CoopReq &q,
+                                 int w, int lane, bool use_tabu, unsigned long long &cost_out, int &pilot_out) {
+    const int s = q.s;
+    const int p = 32 * w + lane;
+    const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
+    uint32_t sl[kSmallBucket], oe[kSmallBucket];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < kSmallBucket; j++) {
+        if (j >= s) break;
+        sl[j] = slot_in_part<REDUCE>(a, q.h[j] ^ hp);
+        oe[j] = bit_of(sh.bits, sl[j]) ? owner[sl[j]] : kNone;
+#pragma unroll
+        for (int k = 0; k < j; k++) ok &= sl[j] != sl[k];
+    }
+    uint64_t cost = 0;
+#pragma unroll
+    for (int j = 0; j < kSmallBucket; j++) {
+        if (j >= s) break;
+        if (oe[j] == kNone) continue;
+        if (use_tabu && in_recent(sh.recent, oe[j] & kOwnerMask)) ok = false;
+        const uint64_t z = oe[j] >> kOwnerShift;
+        cost += z * z;
+    }
+    uint64_t cc = ok ? cost : ~0ull;
+    int pp = ok ? p : 0x7FFFFFFF;
+    for (int off = 16; off; off >>= 1) {
+        const uint64_t oc = __shfl_xor_sync(0xFFFFFFFFu, cc, off);
+        const int op = __shfl_xor_sync(0xFFFFFFFFu, pp, off);
+        if (oc < cc || (oc == cc && op < pp)) { cc = oc; pp = op; }
+    }
+    cost_out = cc;
+    pilot_out = pp;
+}
+
+// Large bucket (hashes in sh.hcache): bit l is set if pilot 32 w + l puts
+// every key on a free slot (self-collisions are checked afterwards).
+template <int REDUCE>
+__device__ unsigned coop_large_share(const SearchArgs &a, const SearchShared &sh, int s, int w, int lane) {
+    const uint64_t hp = a.C * ((uint64_t)(32 * w + lane) ^ a.seed);
+    bool ok = true;
+    for (int j = 0; j < s; j++) {
+        if ((j & 3) == 0 && !__any_sync(0xFFFFFFFFu, ok)) break;
+        if (ok) ok = !bit_of(sh.bits, slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp));
+    }
+    return __ballot_sync(0xFFFFFFFFu, ok);
+}
+
+// Warps 1.. of a drain: score chunks until warp 0 posts kCoopDone.
+template <int REDUCE>
+__device__ void coop_helper(const SearchArgs &a, const SearchShared &sh, const uint32_t *owner, int warp, int lane) {
+    CoopReq &q = *sh.coop;
+    for (;;) {
+        named_barrier(1);
+        const int kind = q.kind;
+        if (kind == kCoopDone) return;
+        if (kind == kCoopGreedy) {
+            const int pl = coop_greedy_share<REDUCE>(a, sh.bits, q, warp, lane);
+            if (lane == 0) q.pilot[warp] = pl;
+        } else if (kind == kCoopLarge) {
+            const unsigned m = coop_large_share<REDUCE>(a, sh, q.s, warp, lane);
+            if (lane == 0) q.mask[warp] = m;
+        } else {
+            unsigned long long c;
+            int pl;
+            coop_evict_share<REDUCE>(a, sh, owner, q, warp, lane, kind == kCoopEvictTabu, c, pl);
+            if (lane == 0) { q.cost[warp] = c; q.pilot[warp] = pl; }
+        }
+        named_barrier(2);
+    }
+}
+
+// Warp 0: posts the bucket (lane j holds key j's hash in myh) and a kind.
+__device__ __forceinline__ void coop_post(const SearchShared &sh, uint64_t myh, int s, int kind, int lane) {
+    CoopReq &q = *sh.coop;
+    if (lane < s) q.h[lane] = myh;
+    if (lane == 0) { q.s = s; q.kind = kind; }
+    __syncwarp();
+    named_barrier(1);
+}
+
+template <int REDUCE>
+__device__ int coop_greedy(const SearchArgs &a, const SearchShared &sh, uint64_t myh, int s, int lane) {
+    CoopReq &q = *sh.coop;
+    coop_post(sh, myh, s, kCoopGreedy, lane);
+    const int mine = coop_greedy_share<REDUCE>(a, sh.bits, q, 0, lane);
+    if (lane == 0) q.pilot[0] = mine;
+    named_barrier(2);
+    for (int w = 0; w < kSearchWarps; w++)
+        if (q.pilot[w] >= 0) return q.pilot[w];
+    return -1;
+}
+
+template <int REDUCE>
+__device__ int coop_evict(const SearchArgs &a, const SearchShared &sh, const uint32_t *owner, uint64_t myh, int s,
+                          int lane, bool use_tabu) {
+    CoopReq &q = *sh.coop;
+    coop_post(sh, myh, s, use_tabu ? kCoopEvictTabu : kCoopEvict, lane);
+    unsigned long long c;
+    int pl;
+    coop_evict_share<REDUCE>(a, sh, owner, q, 0, lane, use_tabu, c, pl);
+    if (lane == 0) { q.cost[0] = c; q.pilot[0] = pl; }
+    named_barrier(2);
+    unsigned long long best = ~0ull;
+    int best_p = -1;
+    for (int w = 0; w < kSearchWarps; w++)
+        if (q.cost[w] < best) { best = q.cost[w]; best_p = q.pilot[w]; }
+    return best_p;
+}
+
+// Large bucket: all warps find the pilots on free slots; warp 0 then checks
+// them for self-collisions, smallest first, through the slot set.
+template <int REDUCE>
+__device__ int coop_greedy_large(const SearchArgs &a, const SearchShared &sh, int s, uint32_t &gen, int lane) {
+    CoopReq &q = *sh.coop;
+    if (lane == 0) { q.s = s; q.kind = kCoopLarge; }
+    named_barrier(1);
+    const unsigned mine = coop_large_share<REDUCE>(a, sh, s, 0, lane);
+    if (lane == 0) q.mask[0] = mine;
+    named_barrier(2);
+    for (int w = 0; w < kSearchWarps; w++) {
+        for (unsigned m = q.mask[w]; m; m &= m - 1) {
+            const int p = 32 * w + __ffs(m) - 1;
+            const uint64_t hp = a.C * ((uint64_t)p ^ a.seed);
+            gen = bump_gen(gen, sh.set, lane);
+            bool bad = false;
+            for (int j = lane; j < s; j += 32)
+                if (!set_insert(sh.set, slot_in_part<REDUCE>(a, sh.hcache[j] ^ hp), gen)) bad = true;
+            if (!__any_sync(0xFFFFFFFFu, bad)) return p;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void coop_done(const SearchShared &sh, int lane) {
+    if (lane == 0) sh.coop->kind = kCoopDone;
+    __syncwarp();
+    named_barrier(1);
+}
+
 // Greedy + hash-evict placement by one warp, over stream positions
 // [first, last) and the waiting buckets in shared memory (deferred or
 // evicted, largest first; ties go to the waiting bucket).  The hashes of
 // the next bucket of the stream are requested while the current one is
-// searched.  Returns a status.
-template <int REDUCE>
-__device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint64_t *order,
-                                  const uint64_t *ohash, uint32_t first, uint32_t last, uint64_t p, int lane,
-                                  unsigned long long &evicted) {
+// searched.  With COOP the other warps score pilots for buckets of up to
+// kSmallBucket keys (they run coop_helper meanwhile).  Returns a status.
+template <int REDUCE, bool COOP>
+__device__ uint32_t search_serial_body(const SearchArgs &a, const SearchShared &sh, uint32_t *owner,
+                                       const uint64_t *order, const uint64_t *ohash, uint32_t first, uint32_t last,
+                                       uint64_t p, int lane, unsigned long long &evicted) {
     const uint64_t gb0 = p * a.B;
     uint32_t next = first, np = *sh.np, rpos = 0, gen = 0;
     if (np > (uint32_t)kPendingCap) return kPartPendingFull;
@@ -423,13 +613,19 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
         } else {
             pf_pos = kNone;
         }
-        int chosen = s <= kSmallBucket ? greedy_small<REDUCE>(a, sh.bits, myh, s, lane)
-                                       : greedy_large<REDUCE>(a, sh, s, gen, lane);
+        const bool coop = COOP && s <= kSmallBucket;
+        int chosen = coop                   ? coop_greedy<REDUCE>(a, sh, myh, s, lane)
+                     : s <= kSmallBucket    ? greedy_small<REDUCE>(a, sh.bits, myh, s, lane)
+                     : COOP                 ? coop_greedy_large<REDUCE>(a, sh, s, gen, lane)
+                                            : greedy_large<REDUCE>(a, sh, s, gen, lane);
         if (chosen < 0) {
-            chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, true);
+            chosen = coop ? coop_evict<REDUCE>(a, sh, owner, myh, s, lane, true)
+                          : evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, true);
             // The tabu only breaks eviction cycles: when it blocks every pilot
             // that does not self-collide, it is ignored for this bucket.
-            if (chosen < 0) chosen = evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, false);
+            if (chosen < 0)
+                chosen = coop ? coop_evict<REDUCE>(a, sh, owner, myh, s, lane, false)
+                              : evict_choice<REDUCE>(a, sh, owner, gb0, myh, s, gen, lane, false);
             if (chosen < 0) { status = kPartNoPilot; break; }
             const uint64_t hp = a.C * ((uint64_t)chosen ^ a.seed);
             // Up to 32 keys: lane j reads the owner of key j's slot, and that
@@ -497,6 +693,15 @@ __device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, u
     return status;
 }
 
+template <int REDUCE, bool COOP>
+__device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint64_t *order,
+                                  const uint64_t *ohash, uint32_t first, uint32_t last, uint64_t p, int lane,
+                                  unsigned long long &evicted) {
+    const uint32_t st = search_serial_body<REDUCE, COOP>(a, sh, owner, order, ohash, first, last, p, lane, evicted);
+    if (COOP) coop_done(sh, lane);   // releases the helpers, whatever the status
+    return st;
+}
+
 // Greedy placement of small buckets (<= kSmallBucket keys) by every warp,
 // in deterministic rounds of kRoundCands candidates (kRoundQ per warp).  In
 // a round each candidate bucket finds its smallest free pilot on the same
@@ -540,11 +745,6 @@ __device__ __forceinline__ uint32_t claim_index(RoundShared &rs, uint32_t sl, bo
     }
     return idx;   // not reached: the table has free entries
 }
-
-template <int REDUCE>
-__device__ uint32_t search_serial(const SearchArgs &a, const SearchShared &sh, uint32_t *owner, const uint64_t *order,
-                                  const uint64_t *ohash, uint32_t first, uint32_t last, uint64_t p, int lane,
-                                  unsigned long long &evicted);
 
 template <int REDUCE>
 __device__ void greedy_rounds(const SearchArgs &a, const SearchShared &sh, RoundShared &rs, uint32_t *owner,
@@ -653,8 +853,10 @@ __device__ void greedy_rounds(const SearchArgs &a, const SearchShared &sh, Round
         // the whole cascade of evicted buckets, before the next round.
         if (*sh.np > 0) {
             if (warp == 0) {
-                const uint32_t st = search_serial<REDUCE>(a, sh, owner, order, ohash, 0, 0, p, lane, evicted);
+                const uint32_t st = search_serial<REDUCE, true>(a, sh, owner, order, ohash, 0, 0, p, lane, evicted);
                 if (lane == 0 && st != kPartOk) *status = st;
+            } else {
+                coop_helper<REDUCE>(a, sh, owner, warp, lane);
             }
             __syncthreads();
             if (*status != kPartOk) break;
@@ -677,7 +879,9 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchA
     sh.recent = sh.pend + kPendingCap;
     __shared__ uint32_t s_part, s_flag, s_nb, s_status, s_np;
     __shared__ RoundShared rs;
+    __shared__ CoopReq s_coop;
     sh.np = &s_np;
+    sh.coop = &s_coop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *owner = a.owner_scratch + (uint64_t)blockIdx.x * a.S;
     uint64_t *order = a.order_scratch + (uint64_t)blockIdx.x * a.B;
@@ -763,11 +967,14 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchA
         for (uint64_t w = tid; w < bits_words; w += blockDim.x) sh.bits[w] = 0;
         if (tid == 0) { s_np = 0; s_status = kPartOk; }
         __syncthreads();
-        // Phase 1: the large buckets, serially, with hash-evict.
+        // Phase 1: the large buckets, serially (warp 0, the other warps
+        // scoring pilots for it), with hash-evict.
         unsigned long long ev = 0;
         if (warp == 0) {
-            const uint32_t st = search_serial<REDUCE>(a, sh, owner, order, ohash, 0, n_large, p, lane, ev);
+            const uint32_t st = search_serial<REDUCE, true>(a, sh, owner, order, ohash, 0, n_large, p, lane, ev);
             if (lane == 0) s_status = st;
+        } else {
+            coop_helper<REDUCE>(a, sh, owner, warp, lane);
         }
         __syncthreads();
         // Phase 2: the small buckets, every warp, greedy; failures wait.
@@ -775,9 +982,13 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pilot_search_kernel(SearchA
             greedy_rounds<REDUCE>(a, sh, rs, owner, order, ohash, n_large, nb, p, warp, lane, ev, &s_status);
         __syncthreads();
         // Phase 3: what waits, serially, with hash-evict.
-        if (warp == 0 && s_status == kPartOk) {
-            const uint32_t st = search_serial<REDUCE>(a, sh, owner, order, ohash, nb, nb, p, lane, ev);
-            if (lane == 0) s_status = st;
+        if (s_status == kPartOk) {
+            if (warp == 0) {
+                const uint32_t st = search_serial<REDUCE, true>(a, sh, owner, order, ohash, nb, nb, p, lane, ev);
+                if (lane == 0) s_status = st;
+            } else {
+                coop_helper<REDUCE>(a, sh, owner, warp, lane);
+            }
         }
         if (warp == 0 && lane == 0) {
             a.status[p] = s_status;
