@@ -182,18 +182,19 @@ int launch_query_u64(const Header &h, const View &v, const uint64_t *keys, uint6
 }
 
 // ------------------------------------------------------------ string keys
-constexpr int kStrThreads = 256;                     // strings per tile and threads per block
+constexpr int kStrThreads = 128;                     // strings per tile and threads per block
 constexpr int kBlkStage = kStrThreads * 64 + 64;     // staged bytes per block
 
-// One string per thread.  The block's 256 contiguous strings are staged
+// One string per thread.  The block's kStrThreads contiguous strings are staged
 // through shared memory with 16-byte loads (every byte below the end of the
 // whole key buffer may be read; only the chunk crossing that end is read
 // byte by byte), then each thread hashes its string from the stage.  A
 // block whose bytes do not fit the stage hashes from global memory.
-// 8 resident blocks per SM (32 registers, a few bytes spilled): the extra
-// blocks hide the stage-then-hash latency, 20 % faster than 6 blocks.
+// 16 resident blocks of 128 threads per SM (32 registers, a few bytes
+// spilled): many small blocks hide the stage-then-hash latency of each
+// block (6 blocks of 256 threads were 26 % slower, 8 of 256 5 % slower).
 template <int GAMMA, int REDUCE, int REMAP, bool WIDE, bool H128>
-__global__ void __launch_bounds__(kStrThreads, 8)
+__global__ void __launch_bounds__(kStrThreads, 16)
 query_bytes_kernel(const View v, const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                    const uint64_t count, void *__restrict__ out) {
     __shared__ __align__(16) uint8_t stage[kBlkStage];
