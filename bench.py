@@ -291,7 +291,8 @@ def run_gpu(args):
                                     if mq == n else f"profiling case: n={n} structure, {mq} sampled member keys"),
                        "n": n, "params": "Default (gamma_3, lambda 3.5, alpha 0.99, CacheLineEF)",
                        "P": info["P"], "S": info["S"], "B": info["B"], "bits_per_key": info["bits_per_key"],
-                       "l2": "inputs larger than L2 (8 GB keys + 4 GB out per step, 286 MB pilots)",
+                       "l2": (f"inputs larger than L2 ({8 * mq / 1e9:.3g} GB keys + {4 * mq / 1e9:.3g} GB out per "
+                              f"step, {info['pilot_bytes'] / 1e6:.0f} MB pilots); no flush"),
                        "parallelism": f"replicas x{ws}"},
             "ns_per_key": 1e9 / (value / ws),
             "query_keys_per_step": mq,
@@ -439,12 +440,13 @@ def run_batched(args, dev, stream):
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         z = torch.cuda.Event(enable_timing=True)
+        reps = max(args.steps, 20)   # one batch is ~0.15 ms: average over enough of them
         a.record(stream)
-        for _ in range(args.steps):
+        for _ in range(reps):
             fn()
         z.record(stream)
         torch.cuda.synchronize()
-        return a.elapsed_time(z) / args.steps
+        return a.elapsed_time(z) / reps
 
     batch_ms = timed(lambda: b.run(arr, k, stream=stream))
     plain_ms = timed(lambda: [N.mphf_query_u64(m, q, o, stream=stream) for m, q, o in items])
