@@ -627,8 +627,14 @@ def cpu_baseline(m, q, sample: int):
     t0 = time.perf_counter()
     ref.query_u64(keys, threads=cores)
     dt = time.perf_counter() - t0
+    one = min(cnt, 1 << 24)   # the one-thread loop on a shorter prefix (about a second)
+    t0 = time.perf_counter()
+    ref.query_u64(keys[:one], threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": cnt / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {cnt} keys of the query stream, same structure, {cores} threads"}
+            "sample": f"first {cnt} keys of the query stream, same structure, {cores} threads",
+            "single_thread": {"value": one / dt1, "unit": UNIT, "ns_per_key": 1e9 * dt1 / one,
+                              "sample": f"first {one} keys, 1 thread"}}
 
 
 # ----------------------------------------------------------- reference arm
