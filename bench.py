@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--batch-mphfs", type=int, default=256)
     ap.add_argument("--batch-config", default="",
                     help="keys_per_thread,threads,blocks_per_sm: fixed batch launch shape instead of autotuning")
+    ap.add_argument("--l2-fetch-granularity", type=int, default=128,
+                    help="L2 fetch granularity (bytes) set once for the whole run through "
+                         "mphf_set_l2_fetch_granularity; 128 speeds up the random pilot gathers")
     ap.add_argument("--query-keys", type=int, default=0,
                     help="query a seeded sample of this many member keys per step instead of all n "
                          "(small profiling case against the full-size structure)")
@@ -80,16 +83,19 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def recorded_traffic(n: int):
+def recorded_traffic(n: int, l2_fetch_granularity: int = 128):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source for this n; else None."""
+    the current kernel source and at the same L2 fetch granularity; else None."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
         return None
     sha = re.search(r"kernel_source_sha:\s*(\w+)", text)
     bpk = re.search(r"dram_bytes_per_key:\s*([0-9.]+)", text)
-    if not sha or not bpk or sha.group(1) != kernel_source_sha():
+    gran = re.search(r"l2_fetch_granularity:\s*(\d+)", text)
+    if not sha or not bpk or not gran or sha.group(1) != kernel_source_sha():
+        return None
+    if int(gran.group(1)) != l2_fetch_granularity:
         return None
     return float(bpk.group(1)) * n
 
@@ -174,6 +180,8 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
     N.load()
+    # One context-wide setting for every leg of the run (query, probe, builds).
+    N.mphf_set_l2_fetch_granularity(args.l2_fetch_granularity)
     n = int(args.n)
 
     def barrier():
@@ -243,7 +251,7 @@ def run_gpu(args):
     alg_bytes = mq * (8 + 4 + 32) + remapped * 64
     kernel_ms = statistics.mean(per_step)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = recorded_traffic(mq)
+    traffic = recorded_traffic(mq, args.l2_fetch_granularity)
 
     # End to end through the C ABI with pinned host buffers.
     e2e = None
@@ -293,7 +301,7 @@ def run_gpu(args):
                        "P": info["P"], "S": info["S"], "B": info["B"], "bits_per_key": info["bits_per_key"],
                        "l2": (f"inputs larger than L2 ({8 * mq / 1e9:.3g} GB keys + {4 * mq / 1e9:.3g} GB out per "
                               f"step, {info['pilot_bytes'] / 1e6:.0f} MB pilots); no flush"),
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}", "l2_fetch_granularity": args.l2_fetch_granularity},
             "ns_per_key": 1e9 / (value / ws),
             "query_keys_per_step": mq,
             "gpu_launches": launches,

@@ -384,6 +384,17 @@ typedef struct {
  * MPHF_ERR_ARG. */
 int mphf_device_view(const mphf_t *m, mphf_view_t *out);
 
+/* Sets the maximum L2 fetch granularity of the calling thread's current
+ * CUDA context to `bytes` (0..128; a performance hint the platform may clamp)
+ * and stores the value in force before the call in *previous (if non-NULL).
+ * No paper counterpart.  For random byte gathers over tables far larger than
+ * L2 (the pilot array), 128 reduces the query time on GB300.  The limit is
+ * context-wide: it applies to every kernel of the process on that device
+ * until it is set again, and it ends with the context.  The library never
+ * changes it by itself.  Errors: MPHF_ERR_ARG (bytes outside 0..128),
+ * MPHF_ERR_CUDA. */
+int mphf_set_l2_fetch_granularity(int bytes, int *previous);
+
 /* Number of kernel launches this library issued since it was loaded
  * (all entry points, all threads). */
 uint64_t mphf_launch_count(void);

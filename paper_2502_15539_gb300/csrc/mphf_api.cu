@@ -573,6 +573,20 @@ const char *mphf_strerror(int code) {
 
 const char *mphf_last_error(void) { return g_err; }
 
+int mphf_set_l2_fetch_granularity(int bytes, int *previous) {
+    if (bytes < 0 || bytes > 128) {
+        set_error("L2 fetch granularity must be 0..128 bytes");
+        return MPHF_ERR_ARG;
+    }
+    size_t old = 0;
+    cudaError_t e = cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity);
+    if (e != cudaSuccess) return cuda_fail(e, "get L2 fetch granularity");
+    e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "set L2 fetch granularity");
+    if (previous) *previous = (int)old;
+    return MPHF_OK;
+}
+
 uint64_t mphf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

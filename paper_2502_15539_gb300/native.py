@@ -125,6 +125,7 @@ SIGNATURES = {
     "mphf_layout": (_i32, [ctypes.POINTER(mphf_params), _u64, ctypes.POINTER(mphf_info_t)]),
     "mphf_gather_probe": (_i32, [_vp, _u64, _vp, _u64, _vp, _vp]),
     "mphf_launch_count": (_u64, []),
+    "mphf_set_l2_fetch_granularity": (_i32, [_i32, ctypes.POINTER(ctypes.c_int)]),
     "mphf_build_u64_noalloc": (_i32, [ctypes.POINTER(mphf_params), _vp, _u64, _vp, _sz, ctypes.POINTER(_sz),
                                       _vp]),
     "mphf_batch_create": (_i32, [ctypes.c_uint32, ctypes.POINTER(_vp)]),
@@ -344,6 +345,14 @@ def mphf_gather_probe(keys: torch.Tensor, table: torch.Tensor, out: torch.Tensor
 
 def mphf_launch_count() -> int:
     return load().mphf_launch_count()
+
+
+def mphf_set_l2_fetch_granularity(nbytes: int) -> int:
+    """Sets the current context's L2 fetch granularity (0..128 bytes; a hint,
+    context-wide); returns the value in force before the call."""
+    prev = ctypes.c_int(0)
+    _check(load().mphf_set_l2_fetch_granularity(int(nbytes), ctypes.byref(prev)), "mphf_set_l2_fetch_granularity")
+    return prev.value
 
 
 def mphf_build_u64_noalloc(keys: torch.Tensor, params: mphf_params | None = None, stream=None) -> bytes:

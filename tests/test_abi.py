@@ -71,6 +71,8 @@ def test_argument_errors_need_no_gpu(lib):
     info = N.mphf_info_t()
     assert lib.mphf_layout(ctypes.byref(p), 0, ctypes.byref(info)) == N.MPHF_ERR_ARG
     lib.mphf_free(None)
+    assert lib.mphf_set_l2_fetch_granularity(129, None) == N.MPHF_ERR_ARG
+    assert lib.mphf_set_l2_fetch_granularity(-1, None) == N.MPHF_ERR_ARG
     assert lib.mphf_strerror(N.MPHF_ERR_DUP_KEYS) == b"duplicate keys"
     assert b"NULL" in lib.mphf_last_error() or lib.mphf_last_error()
 

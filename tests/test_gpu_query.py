@@ -258,3 +258,20 @@ def test_query_bytes_128_bit_hash_matches_oracle(n, params):
     assert np.array_equal(got, want), f"{int((got != want).sum())} mismatches"
     wide = N.mphf_query_bytes_wide(m, qd.cuda(), qo.cuda()).cpu().numpy().view(np.uint64)
     assert np.array_equal(wide, want)
+
+
+def test_l2_fetch_granularity_hint_leaves_results_unchanged():
+    N = need_gpu()
+    n = 200_000
+    ref, blob = oracle_structure(n, 0)
+    m = N.mphf_deserialize(blob)
+    q = W.u64_keys(n, 0)[W.permutation(n, 1)]
+    want = ref.query_u64(W.as_uint64_numpy(q))
+    before = N.mphf_set_l2_fetch_granularity(128)
+    try:
+        assert 0 <= before <= 128
+        assert N.mphf_set_l2_fetch_granularity(128) in (128, 64, 32, 0)   # read back, maybe clamped
+        assert np.array_equal(u32(N.mphf_query_u64(m, q.cuda())), want)
+    finally:
+        N.mphf_set_l2_fetch_granularity(before)
+    assert np.array_equal(u32(N.mphf_query_u64(m, q.cuda())), want)
