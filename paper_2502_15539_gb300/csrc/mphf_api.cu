@@ -510,16 +510,16 @@ int mphf_query_u64_host(mphf_t *m, const uint64_t *keys_host, uint64_t count, ui
     std::lock_guard<std::mutex> lock(m->stage_mu);
     const uint64_t chunk = 1ull << 24;
     cudaError_t e = cudaSuccess;
-    if (m->stage_chunk == 0) {
+    if (m->stage_chunk == 0) {   // resumable: a failed setup keeps what it made for the next call
         for (int i = 0; i < 2 && e == cudaSuccess; i++) {
-            e = cudaMalloc(&m->d_stage_keys[i], chunk * sizeof(uint64_t));
-            if (e == cudaSuccess) e = cudaMalloc(&m->d_stage_out[i], chunk * sizeof(uint32_t));
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_h2d[i], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_q[i], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_d2h[i], cudaEventDisableTiming);
+            if (!m->d_stage_keys[i]) e = cudaMalloc(&m->d_stage_keys[i], chunk * sizeof(uint64_t));
+            if (e == cudaSuccess && !m->d_stage_out[i]) e = cudaMalloc(&m->d_stage_out[i], chunk * sizeof(uint32_t));
+            if (e == cudaSuccess && !m->ev_h2d[i]) e = cudaEventCreateWithFlags(&m->ev_h2d[i], cudaEventDisableTiming);
+            if (e == cudaSuccess && !m->ev_q[i]) e = cudaEventCreateWithFlags(&m->ev_q[i], cudaEventDisableTiming);
+            if (e == cudaSuccess && !m->ev_d2h[i]) e = cudaEventCreateWithFlags(&m->ev_d2h[i], cudaEventDisableTiming);
         }
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->s_h2d, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->s_d2h, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !m->s_h2d) e = cudaStreamCreateWithFlags(&m->s_h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !m->s_d2h) e = cudaStreamCreateWithFlags(&m->s_d2h, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "host query: staging setup");
         m->stage_chunk = chunk;
     }
