@@ -395,6 +395,21 @@ int mphf_device_view(const mphf_t *m, mphf_view_t *out);
  * MPHF_ERR_CUDA. */
 int mphf_set_l2_fetch_granularity(int bytes, int *previous);
 
+/* Fused lookup through the MPHF: out[i] = table[h(keys[i])] for i < count,
+ * where h is the structure's value for a u64 key (Sec. 3.1 Eq. slot,
+ * Sec. 3.4) and table holds n elements of elem_bytes (4 or 8) bytes.  This is
+ * the MPHF's use as the index of a static key set (Sec. 1, Motivation) with
+ * the lookup streamed inside the consuming kernel (Sec. 5): one kernel, the
+ * value never stored.  Non-member keys read some element of the table.
+ * keys_dev: count u64 (device, 8-byte aligned); table_dev: n elements
+ * (device, aligned to elem_bytes; owned by the caller); out_dev: count
+ * elements (device, aligned to elem_bytes).  Any n, including n > 2^32.
+ * Asynchronous on `stream`.  Errors: MPHF_ERR_ARG (NULL or misaligned
+ * pointers, elem_bytes not 4 or 8, a byte-key structure). */
+int mphf_lookup_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
+                    const void *table_dev, uint32_t elem_bytes, void *out_dev,
+                    void *stream);
+
 /* Number of kernel launches this library issued since it was loaded
  * (all entry points, all threads). */
 uint64_t mphf_launch_count(void);

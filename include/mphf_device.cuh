@@ -194,14 +194,26 @@ __device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uin
 // The non-minimal slot (Eq. slot): part S + reduce(hs xor hp(p), S), with
 // the part and bucket taken from hb (Eq. partbucket).  hb = hs except for
 // 128-bit string hashes.
-__device__ __forceinline__ uint64_t slot_hash2(const mphf_view_t &v, uint64_t hb, uint64_t hs) {
-    const uint64_t part = mul_hi(v.P, hb);
+// The two halves of that: the bucket of hb (and its part), and the slot
+// that hs reaches with the bucket's pilot.  Between them sits the one random
+// memory access, pilots[bucket].
+__device__ __forceinline__ uint64_t bucket_index(const mphf_view_t &v, uint64_t hb, uint64_t &part) {
+    part = mul_hi(v.P, hb);
     const uint64_t x = v.P * hb;   // position inside the part, as a fraction of 2^64
     const uint64_t g = v.gamma == MPHF_GAMMA_CUBIC ? bucket_fn<MPHF_GAMMA_CUBIC>(x) : x;
-    const uint64_t b = part * v.B + mul_hi(v.B, g);
-    const uint64_t xp = hs ^ (v.C * ((uint64_t)__ldg(v.pilots + b) ^ v.seed));
+    return part * v.B + mul_hi(v.B, g);
+}
+
+__device__ __forceinline__ uint64_t slot_of_pilot(const mphf_view_t &v, uint64_t hs, uint64_t part, uint32_t pilot) {
+    const uint64_t xp = hs ^ (v.C * ((uint64_t)pilot ^ v.seed));
     const uint64_t r = v.reduce == 0 ? (mul_hi(v.C, xp) & v.s_mask) : mod_barrett(xp, v.barrett, v.S);
     return part * v.S + r;
+}
+
+__device__ __forceinline__ uint64_t slot_hash2(const mphf_view_t &v, uint64_t hb, uint64_t hs) {
+    uint64_t part;
+    const uint64_t b = bucket_index(v, hb, part);
+    return slot_of_pilot(v, hs, part, __ldg(v.pilots + b));
 }
 
 __device__ __forceinline__ uint64_t slot_hash(const mphf_view_t &v, uint64_t h) { return slot_hash2(v, h, h); }
@@ -234,6 +246,42 @@ __device__ __forceinline__ uint32_t eval_u64(const mphf_view_t &v, uint64_t key)
 
 __device__ __forceinline__ uint64_t eval_u64_wide(const mphf_view_t &v, uint64_t key) {
     return eval_hash_wide(v, v.C * key);
+}
+
+// K u64 keys at once, for kernels that want several pilot gathers in flight
+// per thread: all K buckets are computed, then all K pilots requested, and
+// only then are the slots and remap entries resolved.  One key at a time
+// leaves a single random access in flight per thread, since each remap
+// branch ends the compiler's scheduling region.  Results equal eval_u64
+// (eval_u64_wide) key by key.
+template <int K>
+__device__ __forceinline__ void eval_u64_n(const mphf_view_t &v, const uint64_t (&keys)[K], uint32_t (&out)[K]) {
+    uint64_t h[K], part[K], b[K];
+    uint32_t p[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        h[q] = v.C * keys[q];
+        b[q] = bucket_index(v, h[q], part[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) p[q] = __ldg(v.pilots + b[q]);
+#pragma unroll
+    for (int q = 0; q < K; q++) out[q] = eval_slot(v, slot_of_pilot(v, h[q], part[q], p[q]));
+}
+
+template <int K>
+__device__ __forceinline__ void eval_u64_wide_n(const mphf_view_t &v, const uint64_t (&keys)[K], uint64_t (&out)[K]) {
+    uint64_t h[K], part[K], b[K];
+    uint32_t p[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+        h[q] = v.C * keys[q];
+        b[q] = bucket_index(v, h[q], part[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++) p[q] = __ldg(v.pilots + b[q]);
+#pragma unroll
+    for (int q = 0; q < K; q++) out[q] = eval_slot_wide(v, slot_of_pilot(v, h[q], part[q], p[q]));
 }
 
 // A byte-string key (structures built with MPHF_KEY_BYTES), with the

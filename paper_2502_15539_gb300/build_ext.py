@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmphf.so")
-SOURCES = ["mphf_api.cu", "mphf_query.cu", "mphf_build.cu", "mphf_batch.cu", "mphf_serve.cu"]
+SOURCES = ["mphf_api.cu", "mphf_query.cu", "mphf_build.cu", "mphf_batch.cu", "mphf_serve.cu",
+           "mphf_lookup.cu"]
 HEADERS = ["mphf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -126,6 +126,7 @@ SIGNATURES = {
     "mphf_gather_probe": (_i32, [_vp, _u64, _vp, _u64, _vp, _vp]),
     "mphf_launch_count": (_u64, []),
     "mphf_set_l2_fetch_granularity": (_i32, [_i32, ctypes.POINTER(ctypes.c_int)]),
+    "mphf_lookup_u64": (_i32, [_vp, _vp, _u64, _vp, ctypes.c_uint32, _vp, _vp]),
     "mphf_build_u64_noalloc": (_i32, [ctypes.POINTER(mphf_params), _vp, _u64, _vp, _sz, ctypes.POINTER(_sz),
                                       _vp]),
     "mphf_batch_create": (_i32, [ctypes.c_uint32, ctypes.POINTER(_vp)]),
@@ -345,6 +346,24 @@ def mphf_gather_probe(keys: torch.Tensor, table: torch.Tensor, out: torch.Tensor
 
 def mphf_launch_count() -> int:
     return load().mphf_launch_count()
+
+
+def mphf_lookup_u64(m: MPHF, keys: torch.Tensor, table: torch.Tensor, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Fused out[i] = table[h(keys[i])]; table is an int32 or int64 tensor of n elements."""
+    if table.dtype not in (torch.int32, torch.int64):
+        raise ValueError("table must be int32 or int64")
+    if out is None:
+        out = torch.empty(keys.numel(), dtype=table.dtype, device=keys.device)
+    if out.dtype != table.dtype:
+        raise ValueError("out must have the table's dtype")
+    kp = _dev_ptr(keys, keys.dtype, "keys") if _u64_dtype_ok(keys) else None
+    if kp is None:
+        raise ValueError("keys must be int64")
+    _check(load().mphf_lookup_u64(m.handle, kp, keys.numel(), _dev_ptr(table, table.dtype, "table"),
+                                  table.element_size(), _dev_ptr(out, out.dtype, "out"), _stream(stream)),
+           "mphf_lookup_u64")
+    return out
 
 
 def mphf_set_l2_fetch_granularity(nbytes: int) -> int:

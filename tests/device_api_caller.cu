@@ -38,6 +38,22 @@ __global__ void eval_u64_wide_kernel(mphf_view_t v, const uint64_t *keys, uint64
         out[i] = mphf_dev::eval_u64_wide(v, keys[i]);
 }
 
+// K keys per thread through eval_u64_n, with a ragged last group.
+template <int K>
+__global__ void eval_u64_n_kernel(mphf_view_t v, const uint64_t *keys, uint64_t n, uint32_t *out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * K;
+    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * K; base < n; base += stride) {
+        uint64_t k[K];
+        uint32_t val[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) k[q] = base + q < n ? keys[base + q] : keys[0];
+        mphf_dev::eval_u64_n<K>(v, k, val);
+#pragma unroll
+        for (int q = 0; q < K; q++)
+            if (base + q < n) out[base + q] = val[q];
+    }
+}
+
 __global__ void slot_u64_kernel(mphf_view_t v, const uint64_t *keys, uint64_t n, uint64_t *out) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         out[i] = mphf_dev::slot_hash(v, v.C * keys[i]);
@@ -65,6 +81,11 @@ int caller_count_u64(const mphf_view_t *v, const uint64_t *keys, uint64_t n, uin
 
 int caller_eval_u64_wide(const mphf_view_t *v, const uint64_t *keys, uint64_t n, uint64_t *out, void *stream) {
     if (n) eval_u64_wide_kernel<<<grid_for(n), kThreads, 0, (cudaStream_t)stream>>>(*v, keys, n, out);
+    return (int)cudaGetLastError();
+}
+
+int caller_eval_u64_n4(const mphf_view_t *v, const uint64_t *keys, uint64_t n, uint32_t *out, void *stream) {
+    if (n) eval_u64_n_kernel<4><<<grid_for((n + 3) / 4), kThreads, 0, (cudaStream_t)stream>>>(*v, keys, n, out);
     return (int)cudaGetLastError();
 }
 

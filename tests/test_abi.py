@@ -71,6 +71,7 @@ def test_argument_errors_need_no_gpu(lib):
     info = N.mphf_info_t()
     assert lib.mphf_layout(ctypes.byref(p), 0, ctypes.byref(info)) == N.MPHF_ERR_ARG
     lib.mphf_free(None)
+    assert lib.mphf_lookup_u64(None, None, 5, None, 4, None, None) == N.MPHF_ERR_ARG
     assert lib.mphf_set_l2_fetch_granularity(129, None) == N.MPHF_ERR_ARG
     assert lib.mphf_set_l2_fetch_granularity(-1, None) == N.MPHF_ERR_ARG
     assert lib.mphf_strerror(N.MPHF_ERR_DUP_KEYS) == b"duplicate keys"

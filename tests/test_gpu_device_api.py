@@ -37,7 +37,8 @@ def ids(c):
 def caller():
     lib = ctypes.CDLL(caller_library())
     vp = ctypes.c_void_p
-    for name in ("caller_eval_u64", "caller_count_u64", "caller_slot_u64", "caller_eval_u64_wide"):
+    for name in ("caller_eval_u64", "caller_count_u64", "caller_slot_u64", "caller_eval_u64_wide",
+                 "caller_eval_u64_n4"):
         getattr(lib, name).argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
         getattr(lib, name).restype = ctypes.c_int
     lib.caller_eval_bytes.argtypes = [vp, vp, vp, ctypes.c_uint64, vp, vp]
@@ -70,6 +71,10 @@ def test_caller_kernel_matches_oracle(case):
     wide = torch.empty(q.numel(), dtype=torch.int64, device="cuda")
     assert lib.caller_eval_u64_wide(ctypes.byref(view), q.data_ptr(), q.numel(), wide.data_ptr(), stream()) == 0
     assert np.array_equal(wide.cpu().numpy().view(np.uint64), want)
+
+    grouped = torch.empty(q.numel(), dtype=torch.int32, device="cuda")   # 4 keys per thread, ragged tail
+    assert lib.caller_eval_u64_n4(ctypes.byref(view), q.data_ptr(), q.numel(), grouped.data_ptr(), stream()) == 0
+    assert np.array_equal(u32(grouped), want)
 
     slots = torch.empty(q.numel(), dtype=torch.int64, device="cuda")
     assert lib.caller_slot_u64(ctypes.byref(view), q.data_ptr(), q.numel(), slots.data_ptr(), stream()) == 0
@@ -110,3 +115,51 @@ def test_caller_string_kernel_matches_oracle(n, params):
                                  out.data_ptr(), stream()) == 0
     got = u32(out)
     assert np.array_equal(got, ref.query_bytes(qd.numpy(), qo.numpy().astype(np.uint64)))
+
+
+@pytest.mark.parametrize("case", CASES, ids=[ids(c) for c in CASES])
+def test_fused_lookup_reads_the_table_at_the_oracle_value(case):
+    """mphf_lookup_u64: out[i] = table[h(q[i])], h the oracle's value of each key."""
+    N = need_gpu()
+    n, params = case
+    ref, blob = oracle_structure(n, 0, **params)
+    m = N.mphf_deserialize(blob)
+    keys = W.u64_keys(n, 0)
+    q = torch.cat([keys[W.permutation(n, 1)], W.nonmember_u64_keys(max(n // 4, 17), n, 0)])
+    want = ref.query_u64(W.as_uint64_numpy(q)).astype(np.int64)
+    gen = torch.Generator().manual_seed(n)
+    for dtype in (torch.int32, torch.int64):
+        table = torch.randint(-2**31, 2**31 - 1, (n,), generator=gen, dtype=torch.int64).to(dtype)
+        got = N.mphf_lookup_u64(m, q.cuda(), table.cuda()).cpu()
+        assert torch.equal(got, table[torch.from_numpy(want)])
+
+
+@pytest.mark.parametrize("count", [0, 1, 2047, 2048, 2049, 6143, 10_001])
+def test_fused_lookup_ragged_counts(count):
+    N = need_gpu()
+    n = 5000
+    ref, blob = oracle_structure(n, 0)
+    m = N.mphf_deserialize(blob)
+    q = W.u64_keys(count, 9)   # mostly non-members: every key still reads some element
+    table = torch.arange(n, dtype=torch.int64) * 3 + 1
+    out = torch.full((count,), -7, dtype=torch.int64, device="cuda")
+    N.mphf_lookup_u64(m, q.cuda(), table.cuda(), out)
+    want = table[torch.from_numpy(ref.query_u64(W.as_uint64_numpy(q)).astype(np.int64))]
+    assert torch.equal(out.cpu(), want)
+
+
+def test_fused_lookup_argument_errors():
+    N = need_gpu()
+    _, blob = oracle_structure(1000, 0)
+    m = N.mphf_deserialize(blob)
+    lib = N.load()
+    q = W.u64_keys(100, 0).cuda()
+    table = torch.zeros(1000, dtype=torch.int32, device="cuda")
+    out = torch.zeros(100, dtype=torch.int32, device="cuda")
+    assert lib.mphf_lookup_u64(m.handle, q.data_ptr(), 100, table.data_ptr(), 2, out.data_ptr(), None) == N.MPHF_ERR_ARG
+    assert lib.mphf_lookup_u64(m.handle, q.data_ptr() + 4, 10, table.data_ptr(), 4, out.data_ptr(), None) == N.MPHF_ERR_ARG
+    assert lib.mphf_lookup_u64(m.handle, q.data_ptr(), 10, table.data_ptr() + 2, 4, out.data_ptr(), None) == N.MPHF_ERR_ARG
+    data, off = W.strings(torch.arange(50), seed=1)
+    sref = O.OracleMPHF.build_bytes(data.numpy(), off.numpy().astype(np.uint64), threads=2)
+    sm = N.mphf_deserialize(sref.serialize())
+    assert lib.mphf_lookup_u64(sm.handle, q.data_ptr(), 10, table.data_ptr(), 4, out.data_ptr(), None) == N.MPHF_ERR_ARG

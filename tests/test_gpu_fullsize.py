@@ -53,6 +53,13 @@ def test_u64_1e9_keys():
     got = u32(out[idx])
     want = ref.query_u64(W.as_uint64_numpy(q[idx]), threads=CORES)
     assert np.array_equal(got, want)
+    # The fused lookup of the bench's fused leg, on the same stream: a table
+    # whose entry j is j xor a constant, so each output names its value.
+    del out
+    torch.cuda.empty_cache()
+    table = torch.arange(n, dtype=torch.int32, device="cuda") ^ 0x5A5A5A5A
+    looked = N.mphf_lookup_u64(m, q, table)
+    assert np.array_equal(u32(looked[idx]), want ^ np.uint32(0x5A5A5A5A))
 
 
 def test_strings_3e8_keys():
