@@ -35,7 +35,7 @@ QUERY_KERNEL_SOURCES = ["paper_2502_15539_gb300/csrc/mphf_query.cu", "paper_2502
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "query_u64_kernel_n1e9.md")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -66,7 +66,11 @@ def parse():
     ap.add_argument("--query-keys", type=int, default=0,
                     help="query a seeded sample of this many member keys per step instead of all n "
                          "(small profiling case against the full-size structure)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def parse_defaults() -> dict:
+    return vars(parse([]))
 
 
 def kernel_source_sha() -> str:
