@@ -88,9 +88,11 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def recorded_traffic(n: int, l2_fetch_granularity: int = 128):
+def recorded_traffic(structure_n: int, keys_per_launch: int, l2_fetch_granularity: int = 128):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source and at the same L2 fetch granularity; else None."""
+    the current kernel source, on a structure of the same n and at the same L2
+    fetch granularity; else None.  DRAM bytes per key depend on the structure
+    (its pilot array against L2), not on how many keys one launch queries."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
@@ -98,11 +100,12 @@ def recorded_traffic(n: int, l2_fetch_granularity: int = 128):
     sha = re.search(r"kernel_source_sha:\s*(\w+)", text)
     bpk = re.search(r"dram_bytes_per_key:\s*([0-9.]+)", text)
     gran = re.search(r"l2_fetch_granularity:\s*(\d+)", text)
-    if not sha or not bpk or not gran or sha.group(1) != kernel_source_sha():
+    rec_n = re.search(r"structure_n:\s*(\d+)", text)
+    if not sha or not bpk or not gran or not rec_n or sha.group(1) != kernel_source_sha():
         return None
-    if int(gran.group(1)) != l2_fetch_granularity:
+    if int(gran.group(1)) != l2_fetch_granularity or int(rec_n.group(1)) != structure_n:
         return None
-    return float(bpk.group(1)) * n
+    return float(bpk.group(1)) * keys_per_launch
 
 
 class ClockSampler:
@@ -256,7 +259,7 @@ def run_gpu(args):
     alg_bytes = mq * (8 + 4 + 32) + remapped * 64
     kernel_ms = statistics.mean(per_step)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = recorded_traffic(mq, args.l2_fetch_granularity)
+    traffic = recorded_traffic(n, mq, args.l2_fetch_granularity)
 
     # End to end through the C ABI with pinned host buffers.
     e2e = None

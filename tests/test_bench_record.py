@@ -13,11 +13,13 @@ import bench  # noqa: E402
 
 def test_traffic_record_matches_the_current_query_kernel():
     default_gran = bench.parse_defaults()["l2_fetch_granularity"]
-    per_launch = bench.recorded_traffic(10**9, default_gran)
+    per_launch = bench.recorded_traffic(10**9, 10**9, default_gran)
     assert per_launch is not None, "recapture the query kernel: its sources changed since the record"
     # The DRAM bytes per key must exceed the algorithmic minimum (8 key + 4 result + one pilot byte).
     assert 13e9 < per_launch < 200e9
 
 
-def test_traffic_record_is_refused_at_another_granularity():
-    assert bench.recorded_traffic(10**9, 32) is None
+def test_traffic_record_is_refused_at_another_granularity_or_structure():
+    assert bench.recorded_traffic(10**9, 10**9, 32) is None
+    assert bench.recorded_traffic(10**8, 10**8, 128) is None   # a smaller structure: other bytes per key
+    assert bench.recorded_traffic(10**9, 2**26, 128) == 81.88 * 2**26
