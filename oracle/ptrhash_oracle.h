@@ -96,14 +96,16 @@ uint64_t orc_hi(uint64_t a, uint64_t b);
 uint64_t orc_lo(uint64_t a, uint64_t b);
 uint64_t orc_gamma(int gamma, uint64_t x);
 uint64_t orc_hash_u64(uint64_t C, uint64_t k);
-/* parity unpinned against external values: the string hash is this
- * project's own definition (the paper's GxHash is not specified in it); it
- * is pinned only by structural properties in the tests. */
+/* The string hash is this project's own definition (the paper's GxHash is
+ * not specified in it).  Its finishing mixer is SplitMix64's, pinned to that
+ * generator's published outputs through the empty string; the per-word fold
+ * and sum are parity unpinned against external values and pinned only by
+ * structural properties in the tests. */
 uint64_t orc_hash_bytes(const uint8_t *s, uint64_t len, uint64_t seed);
 /* The 128-bit variant: *lo is orc_hash_bytes, *hi the same construction
  * with its own seed tweak and fold constant.  hi picks the part and bucket,
- * lo the slot.  Parity unpinned against external values, like the 64-bit
- * hash; pinned by structural properties in the tests. */
+ * lo the slot.  Pinned like the 64-bit hash: the finishing mixer against
+ * SplitMix64's outputs, the fold (parity unpinned) by properties. */
 void     orc_hash_bytes128(const uint8_t *s, uint64_t len, uint64_t seed, uint64_t *hi, uint64_t *lo);
 uint64_t orc_hp(uint64_t C, uint64_t seed, uint64_t pilot);
 uint64_t orc_reduce(int reduce, uint64_t C, uint64_t x, uint64_t S);

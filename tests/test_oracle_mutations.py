@@ -33,6 +33,9 @@ MUTATIONS = {
     "remap without predecessor fill": ("        else F[j] = prev;\n", "\n"),
     "buckets per part ignore alpha": ("uint64_t B = (uint64_t)ceil(alpha * (double)S / lambda);",
                                       "uint64_t B = (uint64_t)ceil((double)S / lambda);"),
+    "string mixer with a wrong shift": ("    z ^= z >> 27;\n", "    z ^= z >> 28;\n"),
+    "string hash drops the seed from the finish": ("return str_mix(acc ^ (len * K2) ^ seed);",
+                                                   "return str_mix(acc ^ (len * K2));"),
     "128-bit query buckets by the low half": ("orc_part_bucket(&m->L, m->gamma, hb, &part, &b);",
                                               "orc_part_bucket(&m->L, m->gamma, hs, &part, &b);"),
     "128-bit build parts by the low half": ("for (uint64_t i = 0; i < n; i++) part_start[orc_hi(L.P, hb[i]) + 1]++;",

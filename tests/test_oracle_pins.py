@@ -8,6 +8,7 @@ or numbers printed in the paper's tables.
 from __future__ import annotations
 
 import math
+import os
 import random
 from fractions import Fraction
 
@@ -20,6 +21,16 @@ from paper_2502_15539_gb300 import workloads as W
 
 M64 = (1 << 64) - 1
 C_DEFAULT = 0x9E3779B97F4A7C15
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_rows(name):
+    """Whitespace-separated rows of a fixture under tests/golden/ ('#' starts a comment)."""
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [line.split() for line in f if line.strip() and not line.lstrip().startswith("#")]
+
+
+SPACE = {(r[0], int(r[1]), float(r[2]), r[3]): float(r[4]) for r in golden_rows("space_bits_per_key.txt")}
 
 
 def keys_np(n, seed=0):
@@ -139,25 +150,27 @@ def bits_per_key(L, lam_remap):
     return pilots, clef, vec
 
 
-@pytest.mark.parametrize("lam,pilots_paper", [(3.0, 2.67), (3.5, 2.29), (4.0, 2.00)])
-def test_space_matches_table_remap(lam, pilots_paper):
+@pytest.mark.parametrize("lam", [3.0, 3.5, 4.0])
+def test_space_matches_table_remap(lam):
     """Table remap (n = 1e9): pilots 2.67 / 2.29 / 2.00 bits/key, Vec 0.33, CacheLineEF 0.12.
     The table's remap sizes are those of S = 2^18 (the setting of the bucket-function
     figure); with S = 2^18 every figure is reproduced to the printed digits, and the
     parameter rule's S = 2^20 stays within 0.02 of each."""
+    pilots_paper = SPACE[("remap", 10**9, lam, "pilots")]
+    clef_paper, vec_paper = SPACE[("remap", 10**9, 3.5, "clef")], SPACE[("remap", 10**9, 3.5, "vec")]
     L18 = O.layout_for(10**9, lam, 0.99, slots_override=1 << 18)
     p, c, v = bits_per_key(L18, lam)
     assert round(p, 2) == pilots_paper
-    assert round(c, 2) == 0.12 and round(v, 2) == 0.33
+    assert round(c, 2) == clef_paper and round(v, 2) == vec_paper
     L20 = O.layout_for(10**9, lam, 0.99)
     p, c, v = bits_per_key(L20, lam)
-    assert abs(p - pilots_paper) < 0.02 and abs(c - 0.12) < 0.02 and abs(v - 0.33) < 0.02
+    assert abs(p - pilots_paper) < 0.02 and abs(c - clef_paper) < 0.02 and abs(v - vec_paper) < 0.02
 
 
-@pytest.mark.parametrize("lam,remap,total_paper", [(3.0, "vec", 2.99), (3.5, "clef", 2.40),
-                                                   (4.0, "clef", 2.12)])
-def test_space_matches_table_comparison(lam, remap, total_paper):
+@pytest.mark.parametrize("lam,remap", [(3.0, "vec"), (3.5, "clef"), (4.0, "clef")])
+def test_space_matches_table_comparison(lam, remap):
     """Table comparison (3e8 strings): Fast 2.99, Default 2.40, Compact 2.12 bits/key."""
+    total_paper = SPACE[("comparison", 3 * 10**8, lam, "total")]
     L = O.layout_for(3 * 10**8, lam, 0.99)
     p, c, v = bits_per_key(L, lam)
     total = p + (c if remap == "clef" else v)
@@ -377,6 +390,19 @@ def test_serialize_round_trip_and_corruption():
 
 
 # ---------------------------------------------------------------- strings
+def test_empty_string_hash_is_the_splitmix64_mixer_of_the_seed():
+    """The hash finishes with the SplitMix64 mixer (tests/golden/splitmix64_seed0.txt). An empty
+    string has no words and length 0, so its hash is that mixer applied to the seed; with seed
+    k * 0x9E3779B97F4A7C15 it equals the generator's k-th output from state 0. The high half of the
+    128-bit hash is the same construction with seed xor K4."""
+    k4 = 0x47523634D9D6709B
+    for k, want in ((int(r[0]), int(r[1], 16)) for r in golden_rows("splitmix64_seed0.txt")):
+        seed = (k * 0x9E3779B97F4A7C15) & M64
+        assert O.hash_bytes(b"", seed) == want
+        hi, lo = O.hash_bytes128(b"", seed ^ k4)
+        assert hi == want
+
+
 def test_string_hash_properties():
     """Project string hash: depends on every byte, on the length and on the seed."""
     rng = random.Random(9)
