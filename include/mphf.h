@@ -120,7 +120,11 @@ typedef struct {
  * different streams run concurrently (many small structures fill the GPU
  * together).  Errors: MPHF_ERR_ARG, MPHF_ERR_DUP_KEYS (equal u64 keys, or equal
  * strings), MPHF_ERR_OVERFULL, MPHF_ERR_BUILD_FAILED, MPHF_ERR_OOM,
- * MPHF_ERR_CUDA.  On error *out is set to NULL. */
+ * MPHF_ERR_CUDA.  On error *out is set to NULL.
+ * u64 keys are hashed as h = C k (Sec. 3.1), which suits random-looking keys;
+ * strongly structured key sets (multiples of a power of two, arithmetic
+ * progressions) can end in MPHF_ERR_BUILD_FAILED in small layouts, and should
+ * be passed through a bijective 64-bit mixer first. */
 int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
                const uint64_t *offsets_dev, uint64_t n, void *stream,
                mphf_t **out);

@@ -139,8 +139,12 @@ static int is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
  * B = ceil(alpha*S / lambda).  Reading for the "few parts" case: when the
  * power-of-two S would leave more than 5% of all slots beyond n/alpha, the
  * layout switches to reduce = x mod S with P = ceil(n / kpp) and
- * S = max(ceil(n / (alpha P)), ceil(n / P) + 16), bumped by one if it is a
- * power of two.
+ * S = max(ceil(n / (alpha P)), ceil(n / P) + 16), bumped by one if it is
+ * even.  Sec. 3.1 asks for an S that is not a power of two so that x mod S
+ * depends on every bit of x; an even S still passes the low bits of x
+ * through (x mod 2 = (x mod S) mod 2), and keys whose hashes end in t zero
+ * bits (h = C k keeps the trailing zeros of k) would reach only
+ * S / gcd(S, 2^t) slots.  An odd S is never a power of two (S > 16 here).
  * slots_override != 0 forces S (reduce then follows S being a power of 2). */
 int orc_layout_for(uint64_t n, double lambda, double alpha,
                    uint64_t slots_override, orc_layout *out) {
@@ -171,7 +175,7 @@ int orc_layout_for(uint64_t n, double lambda, double alpha,
              * possible; keep at least 16 spare slots per part. */
             uint64_t min_s = (n + P - 1) / P + 16;
             if (S < min_s) S = min_s;
-            if (is_pow2(S)) S += 1;
+            if (S % 2 == 0) S += 1;
             reduce = ORC_REDUCE_MOD;
         }
     }

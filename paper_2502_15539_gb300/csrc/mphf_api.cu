@@ -53,8 +53,11 @@ static bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
 // (at least 80000), S the smallest power of two that holds them, P =
 // ceil(n / (alpha S)), B = ceil(alpha S / lambda).  When that wastes more
 // than 5% of n/alpha slots (few parts), reduce becomes x mod S with P =
-// ceil(n / kpp), S = max(ceil(n / (alpha P)), ceil(n/P) + 16), S not a power
-// of two.  A forced S keeps P = ceil(n / (alpha S)).
+// ceil(n / kpp), S = max(ceil(n / (alpha P)), ceil(n/P) + 16), made odd: the
+// paper wants S not a power of two so that x mod S depends on every bit of x,
+// and an even S would let keys whose hashes share trailing zero bits (h = C k
+// keeps those of k) reach only S / gcd(S, 2^t) slots.  A forced S keeps P =
+// ceil(n / (alpha S)).
 int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_override,
                   uint64_t *P_out, uint64_t *S_out, uint64_t *B_out, int *reduce_out) {
     if (n == 0 || n > kMaxKeys || !(lambda > 0.0) || !(alpha > 0.0) || alpha > 1.0) {
@@ -81,7 +84,7 @@ int choose_layout(uint64_t n, double lambda, double alpha, uint64_t slots_overri
             S = (uint64_t)ceil(nd / (alpha * (double)P));
             const uint64_t floor_s = (n + P - 1) / P + 16;
             if (S < floor_s) S = floor_s;
-            if (is_pow2(S)) S++;
+            if (S % 2 == 0) S++;
             reduce = kReduceMod;
         }
     }

@@ -200,3 +200,16 @@ def test_build_reports_its_phase_times():
     assert sum(phases) <= info["build_ms"] * 1.001
     loaded = N.mphf_info(N.mphf_deserialize(N.mphf_serialize(m)))
     assert loaded["build_ms"] == 0 and loaded["build_search_ms"] == 0
+
+
+@pytest.mark.parametrize("t", [8, 20])
+def test_gpu_build_small_layout_keys_with_trailing_zeros(t):
+    """Keys k 2^t in an x mod S layout (n = 1000): the odd S keeps every slot reachable, so the
+    GPU build succeeds and is a bijection, and it equals the oracle's layout."""
+    N = need_gpu()
+    n = 1000
+    keys = (torch.arange(1, n + 1, dtype=torch.int64) << t).cuda()
+    m = N.mphf_build(keys)
+    info = N.mphf_info(m)
+    assert info["S"] % 2 == 1
+    check_bijection(N, m, keys, n)

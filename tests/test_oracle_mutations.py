@@ -36,6 +36,8 @@ MUTATIONS = {
     "string mixer with a wrong shift": ("    z ^= z >> 27;\n", "    z ^= z >> 28;\n"),
     "string hash drops the seed from the finish": ("return str_mix(acc ^ (len * K2) ^ seed);",
                                                    "return str_mix(acc ^ (len * K2));"),
+    "x mod S layout keeps an even S": ("            if (S % 2 == 0) S += 1;\n",
+                                      "            if (is_pow2(S)) S += 1;\n"),
     "128-bit query buckets by the low half": ("orc_part_bucket(&m->L, m->gamma, hb, &part, &b);",
                                               "orc_part_bucket(&m->L, m->gamma, hs, &part, &b);"),
     "128-bit build parts by the low half": ("for (uint64_t i = 0; i < n; i++) part_start[orc_hi(L.P, hb[i]) + 1]++;",

@@ -185,8 +185,36 @@ def test_layout_small_n_uses_mod_reduce():
         assert L.P * L.S <= 1.05 * n / 0.99 + 18 * L.P  # at most 16 extra spare slots
         assert L.S - -(-n // L.P) >= 16
         if L.reduce == O.REDUCE_MOD:
-            assert L.S & (L.S - 1) != 0
+            assert L.S & (L.S - 1) != 0 and L.S % 2 == 1
     assert O.layout_for(1000).P == 1
+
+
+@pytest.mark.parametrize("n", [1000, 20_000, 100_000, 300_000])
+@pytest.mark.parametrize("t", [1, 8, 20, 32])
+def test_x_mod_s_reaches_every_residue_for_keys_with_trailing_zeros(n, t):
+    """Sec. 3.1 wants x mod S to depend on every bit of x. Keys k 2^t hash to h = C k 2^t,
+    which ends in t zero bits, so for one pilot x = h xor hp keeps hp's low t bits on every
+    key. With an even S those keys would reach only S / gcd(S, 2^t) residues; the layout's S
+    is odd, so brute force over the keys must find residues well spread over [0, S)."""
+    L = O.layout_for(n)
+    assert L.reduce == O.REDUCE_MOD
+    assert math.gcd(L.S, 1 << t) == 1
+    keys = (np.arange(n, dtype=np.uint64) * np.uint64(7919) + np.uint64(1)) << np.uint64(t)   # < 2^64: distinct
+    hp = (C_DEFAULT * 3) & M64
+    residues = {((C_DEFAULT * int(k)) & M64 ^ hp) % L.S for k in keys.tolist()}
+    assert len(residues) >= min(n, L.S) * 0.6
+
+
+@pytest.mark.parametrize("t", [8, 20])
+def test_small_layout_builds_keys_with_trailing_zeros(t):
+    """n = 1000 keys k 2^t: with an even S = 1016 they could reach at most 1016 / 8 = 127
+    slots and no build could succeed; with the odd S every slot is reachable and these
+    builds succeed. (Structured key sets can still defeat the pilot search for other
+    reasons, e.g. t = 3 here; such keys should be passed through a bijective mixer first.)"""
+    n = 1000
+    keys = np.arange(1, n + 1, dtype=np.uint64) << np.uint64(t)
+    ref = O.OracleMPHF.build_u64(keys, threads=2, max_reseeds=3)
+    assert np.array_equal(np.sort(ref.query_u64(keys)), np.arange(n, dtype=np.uint32))
 
 
 # ------------------------------------------------------------------ Sec. 3.4
