@@ -684,7 +684,7 @@ def cpu_baseline(m, q, sample: int):
     t0 = time.perf_counter()
     ref.query_u64(keys, threads=cores)
     dt = time.perf_counter() - t0
-    one = min(cnt, 1 << 24)   # the one-thread loop on a shorter prefix (about a second)
+    one = min(cnt, 1 << 26)   # the one-thread loop on a shorter prefix (about 6 s)
     t0 = time.perf_counter()
     ref.query_u64(keys[:one], threads=1)
     dt1 = time.perf_counter() - t0
