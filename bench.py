@@ -723,12 +723,17 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = sample * args.steps / total
+    L = ref.layout
+    clef_bytes = 64 * -(-(L.P * L.S - n) // 44)   # CacheLineEF: 44 values per 64-byte line
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"plain at scale: n={n} distinct u64 keys, query all n in a seeded random order",
-                   "n": n, "params": "Default (gamma_3, lambda 3.5, alpha 0.99, CacheLineEF)"},
+                   "n": n, "params": "Default (gamma_3, lambda 3.5, alpha 0.99, CacheLineEF)",
+                   "P": L.P, "S": L.S, "B": L.B, "bits_per_key": 8 * (L.P * L.B + clef_bytes) / n,
+                   "l2": "host caches (the oracle runs on the host cores)",
+                   "parallelism": f"oracle threads x{cores}", "l2_fetch_granularity": None},
         "ns_per_key": 1e9 / value,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{sample} keys drawn from the n-key query stream per step, "
