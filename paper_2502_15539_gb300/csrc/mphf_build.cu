@@ -1405,7 +1405,18 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
         }
         built = ok;
     }
-    if (!built) return last_fail;
+    if (!built) {
+        if (last_fail == MPHF_ERR_BUILD_FAILED && key_kind == MPHF_KEY_U64) {
+            // h = C k keeps the structure of lattice-like key sets (arithmetic
+            // progressions, multiples of a power of two), which can defeat the
+            // search under every seed; random-looking keys do not.
+            char msg[512];
+            snprintf(msg, sizeof(msg), "%s; every reseed failed: structured u64 keys should first go through "
+                     "a bijective 64-bit mixer", mphf_last_error());
+            set_error("%s", msg);
+        }
+        return last_fail;
+    }
 
     // Remap (Sec. 3.4).
     CK(cudaEventRecord(ev.a, s));
