@@ -89,6 +89,7 @@ def test_gpu_build_eviction_cap():
     with pytest.raises(N.MphfError) as e:
         N.mphf_build(keys, N.mphf_default_params(max_reseeds=0, evict_mult=0))
     assert e.value.code == N.MPHF_ERR_BUILD_FAILED
+    assert "mixer" in str(e.value)   # the message names the remedy for structured keys
 
 
 @pytest.mark.parametrize("n", [1, 100, 50_000])
