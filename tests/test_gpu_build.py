@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_2502_15539_gb300 import workloads as W
 from tests.gpu_common import need_gpu, u32
 
@@ -213,4 +214,6 @@ def test_gpu_build_small_layout_keys_with_trailing_zeros(t):
     m = N.mphf_build(keys)
     info = N.mphf_info(m)
     assert info["S"] % 2 == 1
+    L = O.layout_for(n)
+    assert (info["P"], info["S"], info["B"]) == (L.P, L.S, L.B)
     check_bijection(N, m, keys, n)
