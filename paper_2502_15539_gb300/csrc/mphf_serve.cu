@@ -25,9 +25,9 @@
 // that observation.
 #include <stdio.h>
 #include <string.h>
-#include <sys/prctl.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -135,6 +135,7 @@ struct mphf_server {
     bool have_first = false;
     int error = MPHF_OK;
     bool stop = false;
+    std::atomic<uint64_t> nudges{0};              // bumped with every cv_work notification
     std::thread dispatcher;
 };
 
@@ -261,14 +262,17 @@ static bool dispatchable(const mphf_server *s, const Req &r) {
     return true;
 }
 
+// How long the dispatcher keeps polling after its last activity before it
+// blocks on the condition variable.  Polling costs one host core while the
+// server is busy; blocking adds a thread wake-up to the next request.
+constexpr std::chrono::microseconds kPollWindow(200);
+
 static void dispatcher_main(mphf_server *s) {
     cudaSetDevice(s->device);
-    // The completion poll below sleeps 5 us at a time; with the default
-    // 50 us timer slack of a Linux thread each of those sleeps would last
-    // about 60 us and add that much to every request's latency.
-    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);   // 1 us
     std::vector<mphf_request> creq;
     std::vector<uint32_t> waits;
+    std::vector<cudaEvent_t> pending;
+    Clock::time_point last_activity = Clock::now();
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
         const bool any_busy = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot &x) { return x.busy; });
@@ -319,12 +323,31 @@ static void dispatcher_main(mphf_server *s) {
             launched = true;
         }
         if (launched) continue;
-        if (std::any_of(s->slots.begin(), s->slots.end(), [](const Slot &x) { return x.busy; })) {
-            lock.unlock();   // poll the in-flight events
-            std::this_thread::sleep_for(std::chrono::microseconds(5));
+        // Nothing more can start now.  Poll for a finished batch or a new
+        // request without holding the lock (holding it between polls starves
+        // the threads that submit), then take it again to act on either.
+        pending.clear();
+        for (const Slot &sl : s->slots)
+            if (sl.busy) pending.push_back(sl.done);
+        Clock::time_point now = Clock::now();
+        if (!pending.empty() || !s->queue.empty()) last_activity = now;
+        if (now - last_activity < kPollWindow) {
+            const uint64_t seen = s->nudges.load(std::memory_order_acquire);
+            // With every slot busy a new request cannot start anyway; waking
+            // for each one would only contend with a burst of submitters.
+            const bool slot_free = pending.size() < s->slots.size();
+            lock.unlock();
+            for (;;) {
+                bool finished = false;
+                for (cudaEvent_t ev : pending)
+                    if (cudaEventQuery(ev) != cudaErrorNotReady) { finished = true; break; }
+                if (finished || (slot_free && s->nudges.load(std::memory_order_acquire) != seen)) break;
+                if (pending.empty() && Clock::now() - last_activity >= kPollWindow) break;
+                std::this_thread::yield();
+            }
             lock.lock();
         } else if (!s->stop) {
-            s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
+            s->cv_work.wait_for(lock, std::chrono::milliseconds(2));   // a queued request restarts the polling
         }
     }
 }
@@ -402,6 +425,7 @@ void mphf_server_free(mphf_server_t *s) {
         std::lock_guard<std::mutex> lock(s->mu);
         s->stop = true;
     }
+    s->nudges.fetch_add(1, std::memory_order_release);
     s->cv_work.notify_all();
     if (s->dispatcher.joinable()) s->dispatcher.join();
     destroy_server(s);
@@ -440,6 +464,7 @@ int mphf_server_remove(mphf_server_t *s, uint32_t id) {
     std::unique_lock<std::mutex> lock(s->mu);
     if (id >= s->entries.size() || s->entries[id].removed) { ptrhash::set_error("unknown structure id"); return MPHF_ERR_ARG; }
     s->entries[id].removed = true;
+    s->nudges.fetch_add(1, std::memory_order_release);
     s->cv_work.notify_all();
     s->cv_done.wait(lock, [&] { return s->entries[id].queued == 0 && s->entries[id].inflight == 0; });
     Entry &e = s->entries[id];
@@ -462,6 +487,7 @@ static int submit_locked(mphf_server *s, const mphf_server_req &r, Clock::time_p
     e.queued++;
     s->queue.push_back(q);
     *ticket = q.ticket;
+    s->nudges.fetch_add(1, std::memory_order_release);
     return MPHF_OK;
 }
 
