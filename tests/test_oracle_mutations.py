@@ -2,7 +2,9 @@
 
 Each case plants one mistake (a dropped term, a wrong operand, a wrong
 index) in a copy of the oracle's C source, builds it, and runs the pin
-tests against it in a subprocess: at least one pin must fail.  The real
+tests (closed forms, invariants, brute force, and the big-integer
+restatement of the query) against it in a subprocess: at least one pin must
+fail.  The real
 oracle is untouched."""
 from __future__ import annotations
 
@@ -42,22 +44,32 @@ MUTATIONS = {
                                               "orc_part_bucket(&m->L, m->gamma, hs, &part, &b);"),
     "128-bit build parts by the low half": ("for (uint64_t i = 0; i < n; i++) part_start[orc_hi(L.P, hb[i]) + 1]++;",
                                             "for (uint64_t i = 0; i < n; i++) part_start[orc_hi(L.P, h[i]) + 1]++;"),
+    # Consistent in the builder and the query, so every structure stays a
+    # bijection: only the independent restatement of Eq. hp / Eq. slot sees them.
+    "pilot hash drops the factor C": ("return C * (pilot ^ seed); }", "return (pilot ^ seed); }"),
+    "slot adds hp instead of xor (builder and query)": [
+        ("uint64_t x = hs ^ orc_hp(m->C, m->seed, pilot);", "uint64_t x = hs + orc_hp(m->C, m->seed, pilot);"),
+        ("orc_reduce(m->L.reduce, m->C, ps->h[j] ^ hp, m->L.S);", "orc_reduce(m->L.reduce, m->C, ps->h[j] + hp, m->L.S);"),
+    ],
 }
+PIN_FILES = ["test_oracle_pins.py", "test_oracle_bigint.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    old, new = MUTATIONS[name]
+    edits = MUTATIONS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor not found: {name}"
+    for old, new in ([edits] if isinstance(edits, tuple) else edits):
+        assert src.count(old) == 1, f"mutation anchor not found: {name}"
+        src = src.replace(old, new)
     mutant = tmp_path / "ptrhash_oracle.c"
-    mutant.write_text(src.replace(old, new))
+    mutant.write_text(src)
     (tmp_path / "ptrhash_oracle.h").write_text(open(os.path.join(ROOT, "oracle", "ptrhash_oracle.h")).read())
     lib = tmp_path / "libmutant.so"
     subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-fPIC", "-shared", "-pthread", "-o", str(lib),
                            str(mutant), "-lm"])
     env = dict(os.environ, PTRHASH_ORACLE_LIB=str(lib))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          *[os.path.join(ROOT, "tests", f) for f in PIN_FILES]],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"no pin caught: {name}\n{res.stdout[-2000:]}"
