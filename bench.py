@@ -63,6 +63,11 @@ def parse(argv=None):
     ap.add_argument("--l2-fetch-granularity", type=int, default=128,
                     help="L2 fetch granularity (bytes) set once for the whole run through "
                          "mphf_set_l2_fetch_granularity; 128 speeds up the random pilot gathers")
+    ap.add_argument("--no-c1", action="store_true", help="skip the n = 1e6 leg")
+    ap.add_argument("--c1-n", type=float, default=1e6)
+    ap.add_argument("--structure", default="",
+                    help="serialized structure file: loaded if it exists (no build in this process), else "
+                         "built and written there (keeps profiled processes free of the builder)")
     ap.add_argument("--query-keys", type=int, default=0,
                     help="query a seeded sample of this many member keys per step instead of all n "
                          "(small profiling case against the full-size structure)")
@@ -198,8 +203,19 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     keys = W.u64_keys(n, seed=0, device=dev)
-    m = N.mphf_build(keys)
+    built_here = True
+    if args.structure and os.path.exists(args.structure):
+        with open(args.structure, "rb") as f:
+            m = N.mphf_deserialize(f.read())
+        built_here = False
+    else:
+        m = N.mphf_build(keys)
+        if args.structure:
+            with open(args.structure, "wb") as f:
+                f.write(N.mphf_serialize(m))
     info = N.mphf_info(m)
+    if info["n"] != n:
+        raise SystemExit(f"{args.structure} holds n={info['n']}, not {n}")
     if 0 < args.query_keys < n:
         mq = args.query_keys
         del keys
@@ -245,13 +261,26 @@ def run_gpu(args):
     total_ms, value = aggregate_ranks(sum(per_step), mq, args.steps, ws, dev)
     ms_per_step = total_ms / args.steps
 
-    # Random-gather probe: same key stream, table the size of the pilot array.
+    # Random-gather probes (the roofline of the pilot gathers), writing to
+    # their own buffer so that `out` keeps the timed query's results.
+    probe_out = torch.empty(mq, dtype=torch.int32, device=dev)
+    # (a) matched: the query's own pilot accesses (its bucket indexes for the
+    # same key stream, gathered from the structure's own pilot array).
+    bidx = N.mphf_bucket_u64(m, q)
+    pilots_ptr = N.mphf_device_view(m).pilots
+    run_matched = lambda: N.mphf_gather_probe_at(bidx, pilots_ptr, info["pilot_bytes"], probe_out, stream=stream)
+    for _ in range(args.warmup):
+        run_matched()
+    matched_ms = statistics.mean(time_steps(run_matched, args.steps))
+    del bidx
+    torch.cuda.empty_cache()
+    # (b) uniform: one byte at a uniformly random index of a table the size of the pilot array.
     table = torch.randint(0, 256, (info["pilot_bytes"],), dtype=torch.uint8, device=dev)
-    run_probe = lambda: N.mphf_gather_probe(q, table, out, stream=stream)
+    run_probe = lambda: N.mphf_gather_probe(q, table, probe_out, stream=stream)
     for _ in range(args.warmup):
         run_probe()
     probe_ms = statistics.mean(time_steps(run_probe, args.steps))
-    del table
+    del table, probe_out
 
     # Roofline of the query kernel (HBM bound): algorithmic bytes per key =
     # 8 (key) + 4 (result) + 32 (the pilot's DRAM sector) + 64 per remapped key.
@@ -285,10 +314,12 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(m, q, args.cpu_sample)
+        cpu = cpu_baseline(m, q, out, args.cpu_sample)
     variants = None if args.no_variants else run_variants(args, m, q, out, stream, time_steps)
     fused = None if args.no_fused else run_fused(args, m, q, out, stream, time_steps, remapped)
     del q, out, m
+    torch.cuda.empty_cache()
+    c1 = None if args.no_c1 else run_c1(args, dev, stream, rank == 0 and ws == 1 and not args.no_cpu_baseline)
     torch.cuda.empty_cache()
     wide = None if args.no_wide else run_wide(args, dev, stream)
     torch.cuda.empty_cache()
@@ -318,12 +349,18 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "alg_bytes_per_key": alg_bytes / mq,
                          "kernel": "query_u64_kernel"},
-            "gather_roofline": {"probe_ms": probe_ms, "query_ms": kernel_ms, "frac": probe_ms / kernel_ms,
-                                "probe": "mphf_gather_probe: same key stream, 1 random byte of a "
-                                         f"{info['pilot_bytes']}-byte table per key",
-                                "pilot_gathers_per_s": mq / (kernel_ms / 1e3),
-                                "key_stream_gbs": 8 * mq / (kernel_ms / 1e3) / 1e9,
-                                "result_stream_gbs": 4 * mq / (kernel_ms / 1e3) / 1e9},
+            "gather_roofline": {
+                "frac": matched_ms / kernel_ms, "probe_ms": matched_ms, "query_ms": kernel_ms,
+                "probe": "mphf_gather_probe_at: the query's own pilot gathers (its bucket indexes for the same "
+                         "key stream, precomputed by mphf_bucket_u64, 8 B in) from the structure's pilot array, "
+                         "u32 out",
+                "probe_gathers_per_s": mq / (matched_ms / 1e3),
+                "query_pilot_gathers_per_s": mq / (kernel_ms / 1e3),
+                "uniform": {"probe_ms": probe_ms, "frac": probe_ms / kernel_ms,
+                            "probe": "mphf_gather_probe: same key stream, 1 byte at a uniformly random index "
+                                     f"of a {info['pilot_bytes']}-byte table per key (no skew)"},
+                "key_stream_gbs": 8 * mq / (kernel_ms / 1e3) / 1e9,
+                "result_stream_gbs": 4 * mq / (kernel_ms / 1e3) / 1e9},
             "remapped_fraction": remapped / mq,
             "build": {"ms": info["build_ms"], "ns_per_key": 1e6 * info["build_ms"] / n,
                       "evictions": info["evictions"], "hash_sort_ms": info["build_hash_sort_ms"],
@@ -331,6 +368,8 @@ def run_gpu(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "structure": "built in this process" if built_here else f"loaded from {args.structure}",
+            "c1": c1,
             "variants": variants,
             "fused": fused,
             "wide": wide,
@@ -341,6 +380,95 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_c1(args, dev, stream, with_oracle: bool):
+    """The plain configuration: n = 1e6 distinct u64 keys (seed 0), Default
+    parameters, GPU-built structure; all n keys queried once in a seeded
+    random order (seed 1).  The query kernel alone, 20 launches, best and
+    median, each timed with CUDA events, both with L2 flushed before every
+    launch (a 256 MB write) and back to back (inputs and structure L2-warm);
+    host to host through mphf_query_u64_host with page-locked buffers; and
+    two L2-regime gather probes over the same key stream as denominators:
+    uniform over a table the size of the pilot array, and the query's own
+    pilot gathers.  The oracle evaluates the same serialized structure on all
+    n keys and the GPU's values must equal it."""
+    import numpy as np
+    import torch
+    from paper_2502_15539_gb300 import native as N
+    from paper_2502_15539_gb300 import workloads as W
+
+    n = int(args.c1_n)
+    keys = W.u64_keys(n, seed=0, device=dev)
+    m = N.mphf_build(keys)
+    info = N.mphf_info(m)
+    q = keys[W.permutation(n, seed=1, device=dev)].contiguous()
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    probe_out = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    reps = 20
+
+    def launches(fn, cold: bool) -> list[float]:
+        for _ in range(5):
+            fn()
+        ts = []
+        for _ in range(reps):
+            if cold:
+                flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    def summary(ts: list[float]) -> dict:
+        return {"best_ms": min(ts), "median_ms": statistics.median(ts),
+                "queries_per_s_best": n / (min(ts) / 1e3), "queries_per_s_median": n / (statistics.median(ts) / 1e3)}
+
+    with torch.cuda.stream(stream):
+        run_q = lambda: N.mphf_query_u64(m, q, out, stream=stream)
+        cold, warm = summary(launches(run_q, True)), summary(launches(run_q, False))
+        table = torch.randint(0, 256, (info["pilot_bytes"],), dtype=torch.uint8, device=dev)
+        uni = summary(launches(lambda: N.mphf_gather_probe(q, table, probe_out, stream=stream), False))
+        bidx = N.mphf_bucket_u64(m, q)
+        ptr = N.mphf_device_view(m).pilots
+        matched = summary(launches(lambda: N.mphf_gather_probe_at(bidx, ptr, info["pilot_bytes"], probe_out,
+                                                                  stream=stream), False))
+    torch.cuda.synchronize()
+    qh = q.cpu().pin_memory()
+    oh = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    for _ in range(3):
+        N.mphf_query_u64_host(m, qh, oh)
+    hts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        N.mphf_query_u64_host(m, qh, oh)
+        hts.append(1e3 * (time.perf_counter() - t0))
+    got = out.cpu().numpy().view(np.uint32)
+    res = {"workload": f"plain: n={n} distinct u64 keys (seed 0), Default params, GPU-built structure "
+                       f"(P={info['P']}, S={info['S']}, {info['pilot_bytes']} pilot bytes); all n keys once in a "
+                       "seeded random order",
+           "kernel_cold_l2": cold, "kernel_warm_l2": warm,
+           "host_to_host": {"best_ms": min(hts), "median_ms": statistics.median(hts),
+                            "queries_per_s_best": n / (min(hts) / 1e3), "h2d_bytes": 8 * n, "d2h_bytes": 4 * n,
+                            "call": "mphf_query_u64_host, page-locked buffers, wall clock"},
+           "gather_roofline": {
+               "matched": dict(matched, frac=matched["median_ms"] / warm["median_ms"],
+                               probe="the query's own pilot gathers (mphf_gather_probe_at)"),
+               "uniform": dict(uni, frac=uni["median_ms"] / warm["median_ms"],
+                               probe=f"uniform random byte of a {info['pilot_bytes']}-byte (L2-resident) table"),
+               "basis": "median of the warm launches"},
+           "host_outputs_equal_device": bool(np.array_equal(oh.numpy().view(np.uint32), got))}
+    if with_oracle:
+        from oracle import oracle as O
+        ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
+        want = ref.query_u64(W.as_uint64_numpy(q), threads=os.cpu_count() or 1)
+        res["parity_checked_keys"] = n
+        res["parity_ok"] = bool(np.array_equal(got, want))
+    del flush, table, bidx, q, out, probe_out, keys, m
+    return res
 
 
 def run_fused(args, m, q, idx, stream, time_steps, remapped):
@@ -515,9 +643,21 @@ def run_batched(args, dev, stream):
         N.mphf_query_u64(m, q, o, stream=stream)
     torch.cuda.synchronize()
     same = all(torch.equal(g, o) for g, (_, _, o) in zip(got, items))
+    # L2-regime gather roofline: the batch's whole key stream, one byte per key
+    # at a uniformly random index of a table as large as all pilot arrays
+    # together (the structures' pilots are L2-resident at this size).
+    pilot_total = sum(N.mphf_info(m)["pilot_bytes"] for m in structs)
+    allq = torch.cat([q for _, q, _ in items])
+    pout = torch.empty(allq.numel(), dtype=torch.int32, device=dev)
+    table = torch.randint(0, 256, (pilot_total,), dtype=torch.uint8, device=dev)
+    probe_ms = timed(lambda: N.mphf_gather_probe(allq, table, pout, stream=stream))
+    del allq, pout, table
     return {"workload": f"{k} structures, n log-uniform [1e3, 1e7] (sum {sum(ns)}), requests log-uniform "
                         f"[1, 1e6] (sum {total}), 90% members",
             "queries_per_s": total / (batch_ms / 1e3), "ms_per_batch": batch_ms,
+            "gather_roofline": {"probe_ms": probe_ms, "frac": probe_ms / batch_ms,
+                                "probe": f"the batch's {total} keys, 1 byte each at a uniformly random index of "
+                                         f"a {pilot_total}-byte table (all pilot arrays together; L2 regime)"},
             "per_request_launches": {"queries_per_s": total / (plain_ms / 1e3), "ms_per_batch": plain_ms},
             "speedup": plain_ms / batch_ms, "autotuned": tuned, "outputs_identical": same,
             "build_ms_total": build_ms, "build_wall_ms": build_wall_ms,
@@ -561,8 +701,15 @@ def run_strings(args, dev, stream):
         bijective = bool(seen.sum().item() == n)
         del seen
     del qd, qo, out, vals
+    peak, peak_kind = measured_peaks()
+    # Algorithmic bytes: the string, its u64 offset, the u32 result and one
+    # 32-byte pilot sector per string.
+    alg = total_bytes + n * (8 + 4 + 32)
+    achieved = alg / (ms / 1e3) / 1e9
     return {"workload": f"{n} strings, length U[16,64] (mean {total_bytes / n:.1f} B), printable ASCII, "
                         "packed + u64 offsets; query order a seeded permutation, re-packed",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "alg_bytes_per_key": alg / n, "kernel": "query_bytes_kernel"},
             "build_ms": info["build_ms"], "build_ns_per_key": 1e6 * info["build_ms"] / n,
             "bits_per_key": info["bits_per_key"], "P": info["P"], "S": info["S"],
             "query_ms": ms, "queries_per_s": n / (ms / 1e3), "ns_per_key": 1e6 * ms / n,
@@ -669,9 +816,10 @@ def run_serving(args, dev):
             "all_resident": roomy}
 
 
-def cpu_baseline(m, q, sample: int):
+def cpu_baseline(m, q, out, sample: int):
     """The oracle, as it stands, on the host cores: one-by-one queries of a
-    prefix of the same query stream against the same structure."""
+    prefix of the same query stream against the same (serialized) structure.
+    Its values are compared with the timed GPU query's output, key by key."""
     import numpy as np
     from oracle import oracle as O
     from paper_2502_15539_gb300 import native as N
@@ -682,14 +830,18 @@ def cpu_baseline(m, q, sample: int):
     keys = W.as_uint64_numpy(q[:cnt])
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    ref.query_u64(keys, threads=cores)
+    want = ref.query_u64(keys, threads=cores)
     dt = time.perf_counter() - t0
+    got = out[:cnt].cpu().numpy().view(np.uint32)
+    mismatches = int(np.count_nonzero(got != want))
+    del want, got
     one = min(cnt, 1 << 26)   # the one-thread loop on a shorter prefix (about 6 s)
     t0 = time.perf_counter()
     ref.query_u64(keys[:one], threads=1)
     dt1 = time.perf_counter() - t0
     return {"value": cnt / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {cnt} keys of the query stream, same structure, {cores} threads",
+            "parity_checked_keys": cnt, "parity_mismatches": mismatches, "parity_ok": mismatches == 0,
             "single_thread": {"value": one / dt1, "unit": UNIT, "ns_per_key": 1e9 * dt1 / one,
                               "sample": f"first {one} keys, 1 thread"}}
 
@@ -729,7 +881,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"plain at scale: n={n} distinct u64 keys, query all n in a seeded random order",
+        "config": {"workload": f"plain at scale: n={n} distinct u64 keys, oracle-built structure; each step "
+                               f"queries a {sample}-key sample of member keys drawn with replacement (seed 1) "
+                               "from the n keys",
                    "n": n, "params": "Default (gamma_3, lambda 3.5, alpha 0.99, CacheLineEF)",
                    "P": L.P, "S": L.S, "B": L.B, "bits_per_key": 8 * (L.P * L.B + clef_bytes) / n,
                    "l2": "host caches (the oracle runs on the host cores)",

@@ -140,6 +140,41 @@ int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
  * MPHF_ERR_ARG, MPHF_ERR_CUDA (launch). */
 int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
                    uint32_t *out_dev, void *stream);
+/* How mphf_query_u64 runs: a batch of at least 2^24 keys against a pilot
+ * array above 72 MiB (n above about 2.5e8 with the Default parameters), with
+ * 16-byte aligned keys and 8-byte aligned out, takes the windowed path of
+ * mphf_query_u64_windowed with its defaults; everything else runs the
+ * single-pass kernel.  Both give the same values.  The windowed path's first
+ * use on a structure allocates its scratch (cudaMalloc, 6 bytes per key of a
+ * chunk of at most 2^27 keys, 805 MB at most), which the structure keeps
+ * until mphf_free; make that first large query outside stream capture.  If
+ * the scratch cannot be allocated, the single-pass kernel runs instead. */
+
+/* The windowed evaluation of the same function (no paper counterpart; the
+ * paper's query reads each key's pilot where it lies, Sec. 3.1).  The pilot
+ * array is cut into W = ceil(P B / window_bytes) byte ranges, each small
+ * enough to stay in L2, and the keys are streamed once per range: the first
+ * pass computes every key's bucket (Eq. partbucket) and keeps it in a 32-bit
+ * stream, each pass reads the pilots of the keys whose bucket lies in its
+ * range, and the last pass computes the slot and remap value (Eq. slot,
+ * Sec. 3.4).  Random DRAM reads of the pilot array become L2 hits, at the
+ * cost of reading the keys twice and 6 bytes of scratch traffic per key and
+ * middle pass.  Results equal mphf_query_u64's, key by key.
+ *   window_bytes  pilot bytes per range; 0: 72 MiB.  W = 1 (window_bytes >=
+ *                 P B) runs the single-pass kernel.
+ *   chunk_keys    keys per chunk (even, at most 2^31; 0: 2^27).  Every chunk
+ *                 reads the pilot array once more; the scratch is 6 bytes per
+ *                 key of a chunk, owned by the structure (allocated on first
+ *                 use, grown when a larger chunk is asked for, freed by
+ *                 mphf_free).  Uses of the scratch from different streams are
+ *                 ordered on the GPU.
+ * keys_dev 16-byte and out_dev 8-byte aligned when W >= 2.  Asynchronous on
+ * `stream`, except that allocating or growing the scratch synchronizes the
+ * device.  Errors: MPHF_ERR_ARG (alignment, odd or oversized chunk, P B >=
+ * 2^32, byte-key structure, n > 2^32), MPHF_ERR_OOM (scratch), MPHF_ERR_CUDA. */
+int mphf_query_u64_windowed(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
+                            uint32_t *out_dev, uint64_t window_bytes, uint64_t chunk_keys,
+                            void *stream);
 
 /* The same for byte-string keys: key i = bytes_dev[offsets_dev[i] ..
  * offsets_dev[i+1]).  offsets_dev: count+1 non-decreasing uint64_t (device).
@@ -215,6 +250,30 @@ int mphf_layout(const mphf_params *params, uint64_t n, mphf_info_t *out);
 int mphf_gather_probe(const uint64_t *keys_dev, uint64_t count,
                       const uint8_t *table_dev, uint64_t table_bytes,
                       uint32_t *out_dev, void *stream);
+
+/* The probe matched to the query's own access pattern: out_dev[i] =
+ * table_dev[idx_dev[i]] (0 where idx_dev[i] >= table_bytes), with the launch
+ * shape of mphf_query_u64, 8 index bytes in and 4 result bytes out per key.
+ * Given the bucket indexes of a query stream (mphf_bucket_u64) and the
+ * structure's own pilot array (mphf_device_view), it makes exactly the
+ * query's pilot gathers, at the same addresses and with the same skew,
+ * without the hashing, slot and remap arithmetic around them: the measured
+ * random-gather bound of that query.  No paper counterpart.
+ * idx_dev: count u64 (device, 16-byte aligned); table_dev: table_bytes bytes
+ * (device); out_dev: count u32 (device, 8-byte aligned).  Asynchronous on
+ * `stream`.  Errors: MPHF_ERR_ARG. */
+int mphf_gather_probe_at(const uint64_t *idx_dev, uint64_t count,
+                         const uint8_t *table_dev, uint64_t table_bytes,
+                         uint32_t *out_dev, void *stream);
+
+/* Bucket of each u64 key as an index into the pilot array: out_dev[i] =
+ * part(k_i) B + bucket(k_i) (Sec. 3.1, Eq. partbucket), the position of the
+ * pilot the query of k_i reads.  keys_dev: count u64 (device, 8-byte
+ * aligned); out_dev: count u64 (device, 8-byte aligned).  Requires a
+ * structure built for MPHF_KEY_U64.  Asynchronous on `stream`.  Errors:
+ * MPHF_ERR_ARG, MPHF_ERR_CUDA. */
+int mphf_bucket_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
+                    uint64_t *out_dev, void *stream);
 
 /* --------------------------------------------------- multi-MPHF batches */
 /* One request of a batch: `count` keys of structure m.  For u64 structures
@@ -338,8 +397,7 @@ void mphf_server_free(mphf_server_t *s);
 /* ------------------------------------------------ build without allocating */
 /* Builds the structure of n <= 65536 distinct u64 keys like mphf_build, but
  * allocates no device memory: all of its device working memory lives in one
- * fixed 8 MiB array that is part of the library image, so every GPU that
- * loads the library holds those 8 MiB until the process exits.  It serves
+ * fixed 8 MiB array that is part of the library's builder module.  It serves
  * callers that may not allocate device memory: code running under a
  * framework that owns all device memory through its own pool and budget,
  * threads where the device-wide synchronization of cudaMalloc/cudaFree would
@@ -349,16 +407,28 @@ void mphf_server_free(mphf_server_t *s);
  *   out_host   host buffer receiving the structure in the serialized format
  *              of mphf_serialize (load it with mphf_deserialize); cap bytes.
  *   needed     set to the serialized size (may be NULL).
- * Synchronous on `stream`.  The result is byte-identical to
- * mphf_serialize(mphf_build(...)) for the same keys and parameters.
- * Errors: MPHF_ERR_CAPACITY if n or the layout exceeds the fixed array;
+ * The result is byte-identical to mphf_serialize(mphf_build(...)) for the
+ * same keys and parameters.
+ * Errors: MPHF_ERR_CAPACITY if n, the number of parts, or the layout's
+ * working memory exceeds the fixed array (the message names the limit);
  * MPHF_ERR_ARG if out_host is NULL or smaller than *needed (retry with a
  * larger buffer); otherwise as mphf_build.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  Every call on a device shares the one array and
- * overwrites what the previous call left there, so calls that overlap on
- * the GPU (from several host threads or streams) race: serialize them. */
+ * When the 8 MiB are taken: the CUDA runtime gives the array device memory
+ * when it loads the builder's module on a device.  With lazy module loading
+ * (the CUDA default) that is the first call into the builder on that device,
+ * this function or mphf_build; with CUDA_MODULE_LOADING=EAGER it is the
+ * creation of the device's context.  A caller that must not allocate later
+ * (a device it will fill up) makes one call early, while memory is free, or
+ * sets CUDA_MODULE_LOADING=EAGER.  The device then holds the array until its
+ * context is destroyed.
+ * The call is synchronous: it waits for its own work on `stream` and copies
+ * the result to out_host, so it must not be issued on a stream that is being
+ * captured into a CUDA graph.  The array's device address is looked up
+ * (cudaGetSymbolAddress) on the first call in each context of a device and
+ * cached; after cudaDeviceReset the next call looks it up again.
+ * Every call on a device shares the one array and overwrites what the
+ * previous call left there, so calls that overlap on the GPU (from several
+ * host threads or streams) race: serialize them. */
 int mphf_build_u64_noalloc(const mphf_params *params, const uint64_t *keys_dev, uint64_t n,
                            void *out_host, size_t cap, size_t *needed, void *stream);
 

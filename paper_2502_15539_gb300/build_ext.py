@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmphf.so")
-SOURCES = ["mphf_api.cu", "mphf_query.cu", "mphf_build.cu", "mphf_batch.cu", "mphf_serve.cu",
+SOURCES = ["mphf_api.cu", "mphf_query.cu", "mphf_window.cu", "mphf_build.cu", "mphf_batch.cu", "mphf_serve.cu",
            "mphf_lookup.cu"]
 HEADERS = ["mphf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

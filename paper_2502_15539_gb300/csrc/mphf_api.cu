@@ -25,6 +25,12 @@ struct mphf {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_q[2] = {}, ev_d2h[2] = {};
     bool owns_device_memory = true;   // false: pilots / remap live in a caller's arena
+    // Scratch of the windowed query (6 bytes per key of a chunk), allocated
+    // on first use and kept; win_done orders its uses on different streams.
+    std::mutex win_mu;
+    uint8_t *d_win = nullptr;
+    uint64_t win_chunk = 0;
+    cudaEvent_t win_done = nullptr;
 };
 
 namespace ptrhash {
@@ -224,6 +230,8 @@ static void free_handle(mphf_t *m) {
     }
     if (m->s_h2d) cudaStreamDestroy(m->s_h2d);
     if (m->s_d2h) cudaStreamDestroy(m->s_d2h);
+    cudaFree(m->d_win);
+    if (m->win_done) cudaEventDestroy(m->win_done);
     cudaSetDevice(dev_prev);
     delete m;
 }
@@ -413,18 +421,101 @@ int mphf_device_view(const mphf_t *m, mphf_view_t *out) {
     return MPHF_OK;
 }
 
-int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
-                   void *stream) {
-    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
-    if (count == 0) return MPHF_OK;
+static int check_query_u64(const mphf_t *m, const uint64_t *keys_dev, const uint32_t *out_dev) {
     if (!keys_dev || !out_dev || ((uintptr_t)keys_dev & 7) || ((uintptr_t)out_dev & 3)) {
         set_error("keys must be 8-byte and out 4-byte aligned device pointers");
         return MPHF_ERR_ARG;
     }
     if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
     if (wide_values(m->hdr.n)) { set_error("n > 2^32: values need the _wide query"); return MPHF_ERR_ARG; }
+    return MPHF_OK;
+}
+
+// The windowed query on the handle's scratch.  Returns MPHF_ERR_OOM (and
+// leaves no CUDA error pending) if the scratch cannot be allocated.
+static int windowed_query(mphf_t *m, const uint64_t *keys, uint64_t count, uint32_t *out, uint64_t W,
+                          uint64_t chunk_keys, cudaStream_t s) {
+    const uint64_t chunk = window_chunk_for(count, chunk_keys);
+    std::lock_guard<std::mutex> lock(m->win_mu);
+    if (m->win_chunk < chunk) {
+        if (m->d_win) {   // grow: cudaFree waits for every earlier use
+            cudaFree(m->d_win);
+            m->d_win = nullptr;
+            m->win_chunk = 0;
+        }
+        cudaError_t e = cudaMalloc(&m->d_win, 6 * chunk);
+        if (e != cudaSuccess) {
+            m->d_win = nullptr;
+            cudaGetLastError();
+            return cuda_fail(e, "windowed query scratch");
+        }
+        m->win_chunk = chunk;
+    }
+    if (!m->win_done) {
+        cudaError_t e = cudaEventCreateWithFlags(&m->win_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "windowed query event");
+    }
+    // A use on another stream may still run: wait for it on the GPU.
+    cudaError_t e = cudaStreamWaitEvent(s, m->win_done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "windowed query: order after the previous use");
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    const int rc = launch_query_u64_windowed(m->hdr, v, keys, count, out, W, chunk, m->d_win, s);
+    e = cudaEventRecord(m->win_done, s);
+    if (rc == MPHF_OK && e != cudaSuccess) return cuda_fail(e, "windowed query: record");
+    return rc;
+}
+
+int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
+                   void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    int rc = check_query_u64(m, keys_dev, out_dev);
+    if (rc) return rc;
+    const uint64_t W = window_plan(m->hdr, count);
+    if (W >= 2 && window_supported(m->hdr, keys_dev, out_dev)) {
+        rc = windowed_query(const_cast<mphf_t *>(m), keys_dev, count, out_dev, W, 0, (cudaStream_t)stream);
+        if (rc != MPHF_ERR_OOM) return rc;   // no room for the scratch: the single pass needs none
+    }
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
     return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, false, (cudaStream_t)stream);
+}
+
+int mphf_query_u64_windowed(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
+                            uint64_t window_bytes, uint64_t chunk_keys, void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    int rc = check_query_u64(m, keys_dev, out_dev);
+    if (rc) return rc;
+    if (chunk_keys % 2 || chunk_keys > (1ull << 31)) {
+        set_error("chunk_keys must be even and at most 2^31 (0: the default)");
+        return MPHF_ERR_ARG;
+    }
+    const uint64_t W = window_count_for(m->hdr.P * m->hdr.B, window_bytes);
+    if (W < 2) {
+        View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+        return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, false, (cudaStream_t)stream);
+    }
+    if (!window_supported(m->hdr, keys_dev, out_dev)) {
+        set_error("windowed query: keys 16-byte and out 8-byte aligned, P B < 2^32");
+        return MPHF_ERR_ARG;
+    }
+    return windowed_query(const_cast<mphf_t *>(m), keys_dev, count, out_dev, W, chunk_keys, (cudaStream_t)stream);
+}
+
+int mphf_bucket_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint64_t *out_dev, void *stream) {
+    if (!m) { set_error("structure is NULL"); return MPHF_ERR_ARG; }
+    if (count == 0) return MPHF_OK;
+    if (!keys_dev || !out_dev || ((uintptr_t)keys_dev & 7) || ((uintptr_t)out_dev & 7)) {
+        set_error("keys and out must be 8-byte aligned device pointers");
+        return MPHF_ERR_ARG;
+    }
+    if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+    View v = make_view(m->hdr, m->d_pilots, m->d_remap);
+    return launch_bucket_u64(m->hdr, v, keys_dev, count, out_dev, sms, (cudaStream_t)stream);
 }
 
 int mphf_query_u64_wide(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint64_t *out_dev,

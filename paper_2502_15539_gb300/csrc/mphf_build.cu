@@ -1511,8 +1511,12 @@ int build_structure(const mphf_params &prm, int key_kind, const void *keys, cons
 // ------------------------------------------------- build without allocating
 // mphf_build_u64_noalloc: the same construction for small key sets, with all
 // device working memory carved out of one fixed, file-scope device array
-// instead of cudaMalloc.  The array is part of the library image, so every
-// GPU that loads the library holds its 8 MiB until the process exits.
+// instead of cudaMalloc.  The array belongs to this translation unit's
+// device module: the CUDA runtime gives it device memory when it loads that
+// module on a device, which under lazy module loading (the default) is the
+// first call into the builder on that device (this entry point or
+// mphf_build), and eagerly at context creation with CUDA_MODULE_LOADING=EAGER.
+// From then on the device holds the 8 MiB until its context is destroyed.
 #include <string.h>
 
 #include <mutex>
@@ -1526,21 +1530,48 @@ constexpr uint64_t kNoAllocMaxParts = 1024;
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 static std::mutex g_noalloc_mu;
-static uint8_t *g_noalloc_base[64] = {};
+struct NoAllocSlot {
+    unsigned long long ctx_id = 0;   // context the address belongs to (0: none yet)
+    uint8_t *base = nullptr;
+};
+static NoAllocSlot g_noalloc[64];
 
-// Device address of the scratch array on device `dev` (current).  In host
-// code the array's name is only a host-side stand-in, so the address is
-// looked up once per device and cached.
+// cuCtxGetId through the runtime's driver entry point, so the library does
+// not link libcuda directly.
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+static unsigned long long current_context_id() {
+    static CtxGetIdFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetIdFn>(p);
+    }();
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array on device `dev`, which must be current
+// with its primary context initialized.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device and context and cached; a new context
+// on the device (after cudaDeviceReset) gets a fresh lookup.
 static int noalloc_scratch(int dev, uint8_t **out) {
     if (dev < 0 || dev >= 64) { set_error("device ordinal %d out of range", dev); return MPHF_ERR_ARG; }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_base[dev]) {
+    const unsigned long long ctx = current_context_id();
+    NoAllocSlot &slot = g_noalloc[dev];
+    if (!slot.base || ctx == 0 || ctx != slot.ctx_id) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_noalloc_base[dev] = static_cast<uint8_t *>(p);
+        slot.base = static_cast<uint8_t *>(p);
+        slot.ctx_id = ctx;
     }
-    *out = g_noalloc_base[dev];
+    *out = slot.base;
     return MPHF_OK;
 }
 
@@ -1578,6 +1609,7 @@ static int build_noalloc(const mphf_params &prm, const uint64_t *keys, uint64_t 
     }
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
+    CK(cudaSetDevice(dev));   // initializes the device's primary context if needed
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     uint8_t *base = nullptr;
     rc = noalloc_scratch(dev, &base);

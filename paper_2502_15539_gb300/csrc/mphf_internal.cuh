@@ -69,6 +69,20 @@ int launch_query_u64_wide(const Header &h, const View &v, const uint64_t *keys, 
 int launch_query_bytes_wide(const Header &h, const View &v, const uint8_t *bytes, const uint64_t *offsets,
                             uint64_t count, uint64_t *out, cudaStream_t s);
 
+// Windowed query (mphf_window.cu): the pilot array in W byte ranges that stay
+// L2-resident, the keys streamed once per range.  window_plan gives the W the
+// automatic path uses for a structure and batch size (1: single pass).
+uint64_t window_count_for(uint64_t nbkt, uint64_t window_bytes);
+uint64_t window_plan(const Header &h, uint64_t count);
+uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys);
+bool window_supported(const Header &h, const uint64_t *keys, const uint32_t *out);
+int launch_query_u64_windowed(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint32_t *out,
+                              uint64_t W, uint64_t chunk, uint8_t *scratch, cudaStream_t s);
+
+// Global bucket index of each u64 key (mphf_query.cu).
+int launch_bucket_u64(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint64_t *out,
+                      int sm_count, cudaStream_t s);
+
 // Key hashes for the builder (mphf_query.cu); out_hi (high halves of the
 // 128-bit string hash) may be NULL.
 int launch_hash_keys(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t C,

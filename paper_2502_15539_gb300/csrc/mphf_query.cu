@@ -347,9 +347,86 @@ gather_probe_kernel(const uint64_t *__restrict__ keys, const uint64_t count, con
     }
 }
 
+// The probe matched to the query's own access pattern: keys are replaced by
+// precomputed table indexes (the query's bucket indexes for the same key
+// stream, mphf_bucket_u64), so the gathers hit the same addresses with the
+// same skew; 8 index bytes in and 4 result bytes out per key, as the query.
+// An index outside the table reads nothing and gives 0.
+__global__ void __launch_bounds__(kThreads)
+gather_probe_at_kernel(const uint64_t *__restrict__ idx, const uint64_t count, const uint8_t *__restrict__ table,
+                       const uint64_t table_bytes, uint32_t *__restrict__ out) {
+    constexpr int K = kKeysPerThread;
+    const uint64_t tile = (uint64_t)blockIdx.x * (kThreads * K);
+    uint64_t b[K];
+    uint32_t p[K];
+    if (tile + kThreads * K <= count) {
+#pragma unroll
+        for (int j = 0; j < K / 2; j++) {
+            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(idx + i));
+            b[2 * j] = ((uint64_t)kk.y << 32) | kk.x;
+            b[2 * j + 1] = ((uint64_t)kk.w << 32) | kk.z;
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) p[q] = b[q] < table_bytes ? (uint32_t)__ldg(table + b[q]) : 0u;
+#pragma unroll
+        for (int j = 0; j < K / 2; j++) {
+            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            __stcs(reinterpret_cast<uint2 *>(out + i), make_uint2(p[2 * j], p[2 * j + 1]));
+        }
+    } else {
+        for (uint64_t i = tile + threadIdx.x; i < count; i += kThreads) {
+            const uint64_t bi = __ldcs(idx + i);
+            out[i] = bi < table_bytes ? (uint32_t)__ldg(table + bi) : 0u;
+        }
+    }
+}
+
+// Global bucket index part B + bucket of each u64 key (Eq. partbucket).
+template <int GAMMA>
+__global__ void bucket_u64_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
+                                  uint64_t *__restrict__ out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t part;
+        __stcs(out + i, (unsigned long long)bucket_of<GAMMA>(v, v.C * __ldcs(keys + i), part));
+    }
+}
+
+int launch_bucket_u64(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint64_t *out,
+                      int sm_count, cudaStream_t s) {
+    const uint64_t want = (count + 255) / 256;
+    const unsigned blocks = (unsigned)(want < (uint64_t)sm_count * 16 ? want : (uint64_t)sm_count * 16);
+    if (h.gamma == MPHF_GAMMA_CUBIC)
+        bucket_u64_kernel<MPHF_GAMMA_CUBIC><<<blocks, 256, 0, s>>>(v, keys, count, out);
+    else
+        bucket_u64_kernel<MPHF_GAMMA_LINEAR><<<blocks, 256, 0, s>>>(v, keys, count, out);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "bucket_u64 launch");
+}
+
 }  // namespace ptrhash
 
 using namespace ptrhash;
+
+extern "C" int mphf_gather_probe_at(const uint64_t *idx_dev, uint64_t count, const uint8_t *table_dev,
+                                    uint64_t table_bytes, uint32_t *out_dev, void *stream) {
+    if (count == 0) return MPHF_OK;
+    if (!idx_dev || !table_dev || !out_dev || table_bytes == 0 || ((uintptr_t)idx_dev % 16) ||
+        ((uintptr_t)out_dev % 8)) {
+        set_error("gather probe: indexes 16-byte aligned, out 8-byte aligned, table non-empty");
+        return MPHF_ERR_ARG;
+    }
+    const uint64_t per_block = (uint64_t)kThreads * kKeysPerThread;
+    const uint64_t blocks = (count + per_block - 1) / per_block;
+    if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
+    gather_probe_at_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(idx_dev, count, table_dev,
+                                                                                table_bytes, out_dev);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "gather probe launch");
+}
 
 extern "C" int mphf_gather_probe(const uint64_t *keys_dev, uint64_t count, const uint8_t *table_dev,
                                  uint64_t table_bytes, uint32_t *out_dev, void *stream) {

@@ -230,7 +230,9 @@ static void admit_locked(mphf_server *s) {
     }
 }
 
-static void complete_locked(mphf_server *s) {
+// Returns whether a batch finished.
+static bool complete_locked(mphf_server *s) {
+    bool any = false;
     for (Entry &e : s->entries)
         if (e.state == kLoading && cudaEventQuery(e.ready) == cudaSuccess) e.state = kResident;
     for (Slot &sl : s->slots) {
@@ -251,8 +253,10 @@ static void complete_locked(mphf_server *s) {
         s->t_last = now;
         sl.reqs.clear();
         sl.busy = false;
+        any = true;
         s->cv_done.notify_all();
     }
+    return any;
 }
 
 static bool dispatchable(const mphf_server *s, const Req &r) {
@@ -272,12 +276,16 @@ static void dispatcher_main(mphf_server *s) {
     std::vector<mphf_request> creq;
     std::vector<uint32_t> waits;
     std::vector<cudaEvent_t> pending;
+    // Activity: a batch launched or finished, or a request arrived.  Queued
+    // requests alone are not activity: one that cannot be dispatched (its
+    // structure waits for room) must not keep the dispatcher polling.
     Clock::time_point last_activity = Clock::now();
+    uint64_t nudges_seen = s->nudges.load(std::memory_order_acquire);
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
         const bool any_busy = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot &x) { return x.busy; });
         if (s->stop && s->queue.empty() && !any_busy) break;
-        complete_locked(s);
+        if (complete_locked(s)) last_activity = Clock::now();
         admit_locked(s);
         bool launched = false;
         for (Slot &sl : s->slots) {
@@ -322,7 +330,10 @@ static void dispatcher_main(mphf_server *s) {
             s->batch_requests += creq.size();
             launched = true;
         }
-        if (launched) continue;
+        if (launched) {
+            last_activity = Clock::now();
+            continue;
+        }
         // Nothing more can start now.  Poll for a finished batch or a new
         // request without holding the lock (holding it between polls starves
         // the threads that submit), then take it again to act on either.
@@ -330,9 +341,10 @@ static void dispatcher_main(mphf_server *s) {
         for (const Slot &sl : s->slots)
             if (sl.busy) pending.push_back(sl.done);
         Clock::time_point now = Clock::now();
-        if (!pending.empty() || !s->queue.empty()) last_activity = now;
+        const uint64_t seen = s->nudges.load(std::memory_order_acquire);
+        if (!pending.empty() || seen != nudges_seen) last_activity = now;   // batches in flight, or a new request
+        nudges_seen = seen;
         if (now - last_activity < kPollWindow) {
-            const uint64_t seen = s->nudges.load(std::memory_order_acquire);
             // With every slot busy a new request cannot start anyway; waking
             // for each one would only contend with a burst of submitters.
             const bool slot_free = pending.size() < s->slots.size();

@@ -1,0 +1,259 @@
+// Windowed query: large batches of u64 keys against a pilot array larger
+// than the L2 cache.
+//
+// The single-pass kernel (mphf_query.cu) makes one random pilot read per key
+// (Sec. 3.1: the one cache line a query touches); past the L2 size nearly
+// every such read goes to DRAM, and the query runs at the device's random
+// DRAM access rate.  Here the pilot array is cut into W byte ranges
+// ("windows") small enough to stay resident in L2, and the keys are streamed
+// once per window; a key reads its pilot in the pass of the window that holds
+// it, so every pilot read after the first touch of its line is an L2 hit.
+// The results are those of Eq. partbucket and Eq. slot, key by key, exactly.
+//
+//   pass 0      keys -> bucket index b (u32 stream) and the pilot of keys in
+//               window 0 (u8 stream); the bucket arithmetic runs only here
+//   pass 1..W-2 (b, carried pilot) -> carried pilot, filling in window w
+//   pass W-1    (key, b, carried pilot) -> the MPHF value (slot, remap)
+//
+// Sequential traffic per key: 13 B in pass 0, 6 B in each middle pass and
+// 17 B in the last, against one random DRAM access in the single pass.
+// Keys are processed in chunks of at most 2^27, so the scratch streams (6 B
+// per key of a chunk, 805 MB) are bounded; every chunk re-reads the pilot
+// windows once (286 MB per 2^27 keys at n = 1e9, about 2 B per key).
+#include "mphf_internal.cuh"
+
+namespace ptrhash {
+
+constexpr int kWinThreads = 256;
+constexpr int kWinKeys = 8;       // keys per thread in the first and last pass
+constexpr int kWinMidKeys = 16;   // keys per thread in the middle passes
+constexpr uint64_t kWindowBytesDefault = 72ull << 20;
+constexpr uint64_t kWindowChunkDefault = 1ull << 27;
+constexpr uint64_t kWindowMinKeys = 1ull << 24;
+
+// hi and lo of the 128-bit product a b for a < 2^32, from two 32 x 32 -> 64
+// products: a b = A + Bv 2^32 with A = a lo32(b), Bv = a hi32(b); the high
+// half is floor((Bv + floor(A / 2^32)) / 2^32), and Bv + floor(A / 2^32) <
+// 2^64 because Bv <= (2^32 - 1)^2.
+__device__ __forceinline__ uint64_t hi32x64(uint32_t a, uint64_t b, uint64_t &lo) {
+    const uint64_t A = (uint64_t)a * (uint32_t)b, Bv = (uint64_t)a * (uint32_t)(b >> 32);
+    lo = (Bv << 32) + A;
+    return (Bv + (A >> 32)) >> 32;
+}
+
+// The bucket index of Eq. partbucket with P, B < 2^32: the same values as
+// bucket_of in the single-pass kernel, with cheaper products.
+template <int GAMMA>
+__device__ __forceinline__ uint64_t window_bucket(const View &v, uint64_t h) {
+    uint64_t x, unused;
+    const uint64_t part = hi32x64((uint32_t)v.P, h, x);
+    return part * v.B + hi32x64((uint32_t)v.B, bucket_fn<GAMMA>(x), unused);
+}
+
+__device__ __forceinline__ bool in_window(uint64_t b, uint64_t lo, uint64_t hi) { return b >= lo && b < hi; }
+
+// Pass 0: bucket index of every key, and the pilot of the keys in [blo, bhi).
+template <int GAMMA>
+__global__ void __launch_bounds__(kWinThreads, 4)
+window_first_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
+                    uint32_t *__restrict__ b32, uint8_t *__restrict__ q, const uint64_t blo, const uint64_t bhi) {
+    constexpr int K = kWinKeys;
+    const uint64_t tile = (uint64_t)blockIdx.x * (kWinThreads * K);
+    if (tile + kWinThreads * K > count) {
+        for (uint64_t i = tile + threadIdx.x; i < count; i += kWinThreads) {
+            const uint64_t b = window_bucket<GAMMA>(v, v.C * __ldcs(keys + i));
+            b32[i] = (uint32_t)b;
+            q[i] = in_window(b, blo, bhi) ? __ldg(v.pilots + b) : 0;
+        }
+        return;
+    }
+    uint64_t b[K];
+    uint32_t p[K];
+#pragma unroll
+    for (int j = 0; j < K / 2; j++) {
+        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
+        const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + i));
+        b[2 * j] = window_bucket<GAMMA>(v, v.C * (((uint64_t)kk.y << 32) | kk.x));
+        b[2 * j + 1] = window_bucket<GAMMA>(v, v.C * (((uint64_t)kk.w << 32) | kk.z));
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) p[k] = in_window(b[k], blo, bhi) ? (uint32_t)__ldg(v.pilots + b[k]) : 0u;
+#pragma unroll
+    for (int j = 0; j < K / 2; j++) {
+        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
+        __stcs(reinterpret_cast<uint2 *>(b32 + i), make_uint2((uint32_t)b[2 * j], (uint32_t)b[2 * j + 1]));
+        __stcs(reinterpret_cast<unsigned short *>(q + i), (unsigned short)(p[2 * j] | (p[2 * j + 1] << 8)));
+    }
+}
+
+// Middle passes: the carried pilot, with the keys of window [blo, bhi) filled in.
+__global__ void __launch_bounds__(kWinThreads, 4)
+window_mid_kernel(const uint8_t *__restrict__ pilots, const uint32_t *__restrict__ b32, const uint64_t count,
+                  const uint8_t *__restrict__ qin, uint8_t *__restrict__ qout, const uint64_t blo, const uint64_t bhi) {
+    constexpr int K = kWinMidKeys;
+    const uint64_t tile = (uint64_t)blockIdx.x * (kWinThreads * K);
+    if (tile + kWinThreads * K > count) {
+        for (uint64_t i = tile + threadIdx.x; i < count; i += kWinThreads) {
+            const uint32_t b = b32[i];
+            qout[i] = in_window(b, blo, bhi) ? __ldg(pilots + b) : qin[i];
+        }
+        return;
+    }
+    uint32_t b[K], p[K], c[K / 2];
+#pragma unroll
+    for (int j = 0; j < K / 2; j++) {
+        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
+        const uint2 bb = __ldcs(reinterpret_cast<const uint2 *>(b32 + i));
+        b[2 * j] = bb.x;
+        b[2 * j + 1] = bb.y;
+        c[j] = __ldcs(reinterpret_cast<const unsigned short *>(qin + i));
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        p[k] = in_window(b[k], blo, bhi) ? (uint32_t)__ldg(pilots + b[k]) : (c[k >> 1] >> (8 * (k & 1))) & 0xFFu;
+#pragma unroll
+    for (int j = 0; j < K / 2; j++) {
+        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
+        __stcs(reinterpret_cast<unsigned short *>(qout + i), (unsigned short)(p[2 * j] | (p[2 * j + 1] << 8)));
+    }
+}
+
+// Last pass: the MPHF value of every key (Eq. slot, Sec. 3.4 remap).  The
+// part is b / B, taken as hi(b M) with M = ceil(2^64 / B), exact for b, B <
+// 2^32 (the error b (M - 2^64 / B) / 2^64 < 2^-32 < 1 / B cannot carry the
+// quotient over an integer).  hp(p) = C (p xor seed) comes from a table of
+// the 256 pilot values in shared memory.
+template <int REDUCE, int REMAP>
+__global__ void __launch_bounds__(kWinThreads, 4)
+window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
+                   const uint32_t *__restrict__ b32, const uint8_t *__restrict__ qin, uint32_t *__restrict__ out,
+                   const uint64_t blo, const uint64_t bhi, const uint64_t part_magic) {
+    constexpr int K = kWinKeys;
+    __shared__ uint64_t hp[256];
+    hp[threadIdx.x] = v.C * ((uint64_t)threadIdx.x ^ v.seed);   // kWinThreads == 256
+    __syncthreads();
+    auto value = [&](uint64_t key, uint32_t b, uint32_t pilot) -> uint32_t {
+        uint64_t unused;
+        const uint64_t part = v.B == 1 ? b : hi32x64(b, part_magic, unused);
+        const uint64_t s = part * v.S + reduce_slot<REDUCE>(v, (v.C * key) ^ hp[pilot]);
+        if (s < v.n) return (uint32_t)s;
+        const uint32_t j = (uint32_t)(s - v.n);
+        if constexpr (REMAP == kRemapClef) return clef_get(static_cast<const uint8_t *>(v.remap), j);
+        else return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+    };
+    const uint64_t tile = (uint64_t)blockIdx.x * (kWinThreads * K);
+    if (tile + kWinThreads * K > count) {
+        for (uint64_t i = tile + threadIdx.x; i < count; i += kWinThreads) {
+            const uint32_t b = b32[i];
+            out[i] = value(__ldcs(keys + i), b, in_window(b, blo, bhi) ? __ldg(v.pilots + b) : qin[i]);
+        }
+        return;
+    }
+    uint64_t k[K];
+    uint32_t b[K], p[K], c[K / 2];
+#pragma unroll
+    for (int j = 0; j < K / 2; j++) {
+        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
+        const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + i));
+        k[2 * j] = ((uint64_t)kk.y << 32) | kk.x;
+        k[2 * j + 1] = ((uint64_t)kk.w << 32) | kk.z;
+        const uint2 bb = __ldcs(reinterpret_cast<const uint2 *>(b32 + i));
+        b[2 * j] = bb.x;
+        b[2 * j + 1] = bb.y;
+        c[j] = __ldcs(reinterpret_cast<const unsigned short *>(qin + i));
+    }
+#pragma unroll
+    for (int q = 0; q < K; q++)
+        p[q] = in_window(b[q], blo, bhi) ? (uint32_t)__ldg(v.pilots + b[q]) : (c[q >> 1] >> (8 * (q & 1))) & 0xFFu;
+#pragma unroll
+    for (int j = 0; j < K / 2; j++) {
+        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
+        __stcs(reinterpret_cast<uint2 *>(out + i),
+               make_uint2(value(k[2 * j], b[2 * j], p[2 * j]), value(k[2 * j + 1], b[2 * j + 1], p[2 * j + 1])));
+    }
+}
+
+static_assert(kWinThreads == 256, "the last pass fills its 256-entry hp table with one thread per pilot value");
+
+template <int GAMMA, int REDUCE, int REMAP>
+static int run_windows(const View &v, const uint64_t *keys, uint64_t count, uint32_t *out, uint64_t W,
+                       uint64_t chunk, uint64_t part_magic, uint8_t *scratch, cudaStream_t s) {
+    const uint64_t nbkt = v.P * v.B;
+    uint32_t *b32 = reinterpret_cast<uint32_t *>(scratch);
+    uint8_t *qa = scratch + 4 * chunk, *qb = qa + chunk;
+    for (uint64_t c0 = 0; c0 < count; c0 += chunk) {
+        const uint64_t cnt = count - c0 < chunk ? count - c0 : chunk;
+        const unsigned blocks = (unsigned)((cnt + kWinThreads * kWinKeys - 1) / (kWinThreads * kWinKeys));
+        const unsigned mid_blocks = (unsigned)((cnt + kWinThreads * kWinMidKeys - 1) / (kWinThreads * kWinMidKeys));
+        uint8_t *qi = qa, *qo = qb;
+        for (uint64_t w = 0; w < W; w++) {
+            const uint64_t blo = nbkt * w / W, bhi = nbkt * (w + 1) / W;
+            if (w == 0)
+                window_first_kernel<GAMMA><<<blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qo, blo, bhi);
+            else if (w + 1 < W)
+                window_mid_kernel<<<mid_blocks, kWinThreads, 0, s>>>(v.pilots, b32, cnt, qi, qo, blo, bhi);
+            else
+                window_last_kernel<REDUCE, REMAP><<<blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qi,
+                                                                               out + c0, blo, bhi, part_magic);
+            count_launch();
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "windowed query launch");
+            uint8_t *t = qi;
+            qi = qo;
+            qo = t;
+        }
+    }
+    return MPHF_OK;
+}
+
+uint64_t window_count_for(uint64_t nbkt, uint64_t window_bytes) {
+    if (window_bytes == 0) window_bytes = kWindowBytesDefault;
+    return (nbkt + window_bytes - 1) / window_bytes;
+}
+
+uint64_t window_plan(const Header &h, uint64_t count) {
+    const uint64_t W = window_count_for(h.P * h.B, 0);
+    return (W >= 2 && count >= kWindowMinKeys) ? W : 1;
+}
+
+uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys) {
+    uint64_t chunk = chunk_keys ? chunk_keys : kWindowChunkDefault;
+    const uint64_t even = count + (count & 1);
+    return chunk < even ? chunk : even;
+}
+
+bool window_supported(const Header &h, const uint64_t *keys, const uint32_t *out) {
+    const uint64_t nbkt = h.P * h.B;
+    return h.B > 0 && h.P < (1ull << 32) && h.B < (1ull << 32) && nbkt < (1ull << 32) && ((uintptr_t)keys % 16) == 0 &&
+           ((uintptr_t)out % 8) == 0;
+}
+
+template <int GAMMA, int REDUCE>
+static int run_windows_remap(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint32_t *out,
+                             uint64_t W, uint64_t chunk, uint64_t part_magic, uint8_t *scratch, cudaStream_t s) {
+    if (h.remap == MPHF_REMAP_VEC)
+        return run_windows<GAMMA, REDUCE, kRemapVec>(v, keys, count, out, W, chunk, part_magic, scratch, s);
+    return run_windows<GAMMA, REDUCE, kRemapClef>(v, keys, count, out, W, chunk, part_magic, scratch, s);
+}
+
+// scratch: 6 chunk bytes of device memory (the bucket stream and two
+// carried-pilot streams of one chunk), at least 8-byte aligned.
+int launch_query_u64_windowed(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint32_t *out,
+                              uint64_t W, uint64_t chunk, uint8_t *scratch, cudaStream_t s) {
+    if (W < 2 || chunk < 2 || chunk % 2 || chunk > (1ull << 31) || !window_supported(h, keys, out)) {
+        set_error("windowed query: W >= 2, an even chunk of at most 2^31 keys, P B < 2^32, aligned buffers");
+        return MPHF_ERR_ARG;
+    }
+    // M = ceil(2^64 / B) gives the part of a bucket index (B >= 2).
+    const uint64_t part_magic = h.B == 1 ? 0 : (uint64_t)((((unsigned __int128)1 << 64) + h.B - 1) / h.B);
+    const bool cubic = h.gamma == MPHF_GAMMA_CUBIC, pow2 = h.reduce == kReducePow2;
+    if (cubic && pow2)
+        return run_windows_remap<MPHF_GAMMA_CUBIC, kReducePow2>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
+    if (cubic)
+        return run_windows_remap<MPHF_GAMMA_CUBIC, kReduceMod>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
+    if (pow2)
+        return run_windows_remap<MPHF_GAMMA_LINEAR, kReducePow2>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
+    return run_windows_remap<MPHF_GAMMA_LINEAR, kReduceMod>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
+}
+
+}  // namespace ptrhash

@@ -115,6 +115,7 @@ SIGNATURES = {
     "mphf_query_u64": (_i32, [_vp, _vp, _u64, _vp, _vp]),
     "mphf_query_bytes": (_i32, [_vp, _vp, _vp, _u64, _vp, _vp]),
     "mphf_query_u64_phf": (_i32, [_vp, _vp, _u64, _vp, _vp]),
+    "mphf_query_u64_windowed": (_i32, [_vp, _vp, _u64, _vp, _u64, _u64, _vp]),
     "mphf_query_u64_host": (_i32, [_vp, _vp, _u64, _vp, _vp]),
     "mphf_serialize": (_i32, [_vp, _vp, _sz, ctypes.POINTER(_sz)]),
     "mphf_deserialize": (_i32, [_vp, _sz, ctypes.POINTER(_vp)]),
@@ -124,6 +125,8 @@ SIGNATURES = {
     "mphf_last_error": (ctypes.c_char_p, []),
     "mphf_layout": (_i32, [ctypes.POINTER(mphf_params), _u64, ctypes.POINTER(mphf_info_t)]),
     "mphf_gather_probe": (_i32, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "mphf_gather_probe_at": (_i32, [_vp, _u64, _vp, _u64, _vp, _vp]),
+    "mphf_bucket_u64": (_i32, [_vp, _vp, _u64, _vp, _vp]),
     "mphf_launch_count": (_u64, []),
     "mphf_set_l2_fetch_granularity": (_i32, [_i32, ctypes.POINTER(ctypes.c_int)]),
     "mphf_lookup_u64": (_i32, [_vp, _vp, _u64, _vp, ctypes.c_uint32, _vp, _vp]),
@@ -285,6 +288,17 @@ def mphf_query_u64(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None,
     return out
 
 
+def mphf_query_u64_windowed(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None, window_bytes: int = 0,
+                            chunk_keys: int = 0, stream=None) -> torch.Tensor:
+    """The windowed evaluation (0: the defaults); the same values as mphf_query_u64."""
+    if out is None:
+        out = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+    _check(load().mphf_query_u64_windowed(m.handle, _dev_ptr(keys, torch.int64, "keys"), keys.numel(),
+                                          _dev_ptr(out, torch.int32, "out"), window_bytes, chunk_keys,
+                                          _stream(stream)), "mphf_query_u64_windowed")
+    return out
+
+
 def mphf_query_u64_phf(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     if out is None:
         out = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
@@ -341,6 +355,24 @@ def mphf_gather_probe(keys: torch.Tensor, table: torch.Tensor, out: torch.Tensor
     _check(load().mphf_gather_probe(_dev_ptr(keys, torch.int64, "keys"), keys.numel(),
                                     _dev_ptr(table, torch.uint8, "table"), table.numel(),
                                     _dev_ptr(out, torch.int32, "out"), _stream(stream)), "mphf_gather_probe")
+    return out
+
+
+def mphf_gather_probe_at(idx: torch.Tensor, table_ptr: int, table_bytes: int, out: torch.Tensor,
+                         stream=None) -> torch.Tensor:
+    """out[i] = table[idx[i]]; table_ptr is a device address (for example the
+    pilots of mphf_device_view) holding table_bytes bytes."""
+    _check(load().mphf_gather_probe_at(_dev_ptr(idx, torch.int64, "idx"), idx.numel(), table_ptr, table_bytes,
+                                       _dev_ptr(out, torch.int32, "out"), _stream(stream)), "mphf_gather_probe_at")
+    return out
+
+
+def mphf_bucket_u64(m: MPHF, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Index into the pilot array of each key's bucket (int64 tensor)."""
+    if out is None:
+        out = torch.empty(keys.numel(), dtype=torch.int64, device=keys.device)
+    _check(load().mphf_bucket_u64(m.handle, _dev_ptr(keys, torch.int64, "keys"), keys.numel(),
+                                  _dev_ptr(out, torch.int64, "out"), _stream(stream)), "mphf_bucket_u64")
     return out
 
 

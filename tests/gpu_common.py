@@ -31,3 +31,17 @@ def oracle_structure(n: int, key_seed: int = 0, **params) -> tuple[O.OracleMPHF,
 
 def u32(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint32)
+
+
+def oracle_values_of(N, m, keys=None, data=None, offsets=None) -> np.ndarray:
+    """The oracle's evaluation of a library structure: its serialized bytes
+    are loaded by the oracle's own reader and queried one key at a time, so a
+    GPU-built structure is checked against the formula, not only for being a
+    bijection (Sec. 3.2)."""
+    ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
+    if keys is not None:
+        k = W.as_uint64_numpy(keys)
+        return ref.query_u64(k, threads=16 if len(k) >= 10**5 else 1)
+    d = data.detach().cpu().numpy()
+    o = offsets.detach().cpu().numpy().astype(np.uint64)
+    return ref.query_bytes(d, o, threads=16 if len(o) > 10**5 else 1)

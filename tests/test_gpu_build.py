@@ -1,6 +1,7 @@
 """The library's own GPU builder: every structure it builds must be a
-bijection onto [0, n) for its keys, whatever the layout (Sec. 3.2); its
-errors follow the same rules as the oracle's."""
+bijection onto [0, n) for its keys, whatever the layout (Sec. 3.2), and the
+GPU's values must equal the oracle's evaluation of the same serialized
+structure; its errors follow the same rules as the oracle's."""
 from __future__ import annotations
 
 import numpy as np
@@ -9,14 +10,23 @@ import torch
 
 from oracle import oracle as O
 from paper_2502_15539_gb300 import workloads as W
-from tests.gpu_common import need_gpu, u32
+from tests.gpu_common import need_gpu, oracle_values_of, u32
 
 pytestmark = pytest.mark.gpu
 
 
 def check_bijection(N, m, keys_dev, n):
+    """A bijection onto [0, n), and element-wise the oracle's values for the
+    same serialized structure."""
     got = u32(N.mphf_query_u64(m, keys_dev))
     assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+    assert np.array_equal(got, oracle_values_of(N, m, keys=keys_dev))
+
+
+def check_strings(N, m, data, off, n):
+    got = u32(N.mphf_query_bytes(m, data, off))
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+    assert np.array_equal(got, oracle_values_of(N, m, data=data, offsets=off))
 
 
 BUILD_CASES = [
@@ -37,7 +47,9 @@ def test_gpu_build_is_bijective(n, params):
     assert info["n"] == n
     check_bijection(N, m, keys, n)
     other = W.nonmember_u64_keys(1000, n, 1).cuda()
-    assert u32(N.mphf_query_u64(m, other)).max() < n
+    vals = u32(N.mphf_query_u64(m, other))
+    assert vals.max() < n
+    assert np.array_equal(vals, oracle_values_of(N, m, keys=other))
     # The serialized structure reloads to the same function.
     m2 = N.mphf_deserialize(N.mphf_serialize(m))
     assert np.array_equal(u32(N.mphf_query_u64(m2, keys)), u32(N.mphf_query_u64(m, keys)))
@@ -62,6 +74,7 @@ def test_gpu_build_remap_invariants():
     slots = u32(N.mphf_query_u64_phf(m, keys)).astype(np.int64)
     final = u32(N.mphf_query_u64(m, keys)).astype(np.int64)
     assert len(np.unique(slots)) == n
+    assert np.array_equal(final, oracle_values_of(N, m, keys=keys).astype(np.int64))
     hi = slots >= n
     order = np.argsort(slots[hi])
     taken = np.zeros(n, bool)
@@ -98,8 +111,7 @@ def test_gpu_build_strings_bijective(n):
     N = need_gpu()
     data, off = W.strings(torch.arange(n), seed=6)
     m = N.mphf_build(data.cuda(), offsets=off.cuda())
-    got = u32(N.mphf_query_bytes(m, data.cuda(), off.cuda()))
-    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+    check_strings(N, m, data.cuda(), off.cuda(), n)
 
 
 def test_gpu_build_duplicate_strings_rejected():
@@ -135,8 +147,7 @@ def test_sharded_string_build_is_identical():
     whole = N.mphf_serialize(N.mphf_build(data, offsets=off))
     m = N.mphf_build(data, N.mphf_default_params(shard_keys=40_000), offsets=off)   # P = 3: three shards
     assert N.mphf_serialize(m) == whole
-    got = u32(N.mphf_query_bytes(m, data, off))
-    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+    check_strings(N, m, data, off, n)
 
 
 @pytest.mark.parametrize("n", [1, 1000, 300_000])
@@ -150,8 +161,7 @@ def test_gpu_build_with_128_bit_string_hash(n):
     m = N.mphf_build(data, N.mphf_default_params(hash128=1), offsets=off)
     blob = N.mphf_serialize(m)
     assert int.from_bytes(blob[28:32], "little") == 1
-    got = u32(N.mphf_query_bytes(m, data, off))
-    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+    check_strings(N, m, data, off, n)
     if n >= 300_000:   # P = 3: three shards
         sharded = N.mphf_build(data, N.mphf_default_params(hash128=1, shard_keys=40_000), offsets=off)
         assert N.mphf_serialize(sharded) == blob

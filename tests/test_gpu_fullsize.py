@@ -46,9 +46,12 @@ def test_u64_1e9_keys():
     q = keys[W.permutation(n, seed=1, device="cuda")]
     del keys
     torch.cuda.empty_cache()
-    out = N.mphf_query_u64(m, q)
+    out = N.mphf_query_u64(m, q)   # the windowed path at this size
     torch.cuda.synchronize()
     assert_bijection_on_device(out, n)
+    single = N.mphf_query_u64_windowed(m, q, window_bytes=1 << 40)   # one window: the single-pass kernel
+    assert torch.equal(out, single)
+    del single
     idx = sample_positions(n).cuda()
     got = u32(out[idx])
     want = ref.query_u64(W.as_uint64_numpy(q[idx]), threads=CORES)

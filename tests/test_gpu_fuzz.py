@@ -5,8 +5,9 @@ Each case draws n, lambda, alpha, gamma, the remap kind, the key kind
 count (power of two or not, hence both reduce modes), builds the structure
 with the oracle and checks every query path of the library on it: 32-bit
 and 64-bit results, members and non-members.  The library's own builder
-then builds the same key set under the same parameters and must give a
-bijection (Sec. 3.2)."""
+then builds the same key set under the same parameters: that structure must
+be a bijection (Sec. 3.2), and the oracle, loading its serialized bytes,
+must give the GPU's values on members and non-members alike."""
 from __future__ import annotations
 
 import random
@@ -17,7 +18,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2502_15539_gb300 import workloads as W
-from tests.gpu_common import need_gpu, u32
+from tests.gpu_common import need_gpu, oracle_values_of, u32
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +57,7 @@ def test_random_layout_matches_oracle(case):
         assert np.array_equal(N.mphf_query_u64_wide(m, q.cuda()).cpu().numpy().view(np.uint64), want)
         gpu = N.mphf_build(keys.cuda(), N.mphf_default_params(**p))
         got = u32(N.mphf_query_u64(gpu, keys.cuda()))
+        assert np.array_equal(u32(N.mphf_query_u64(gpu, q.cuda())), oracle_values_of(N, gpu, keys=q))
     else:
         h128 = 1 if kind == "bytes128" else 0
         data, off = W.strings(torch.arange(n), seed=ks)
@@ -68,4 +70,6 @@ def test_random_layout_matches_oracle(case):
         assert np.array_equal(N.mphf_query_bytes_wide(m, qd.cuda(), qo.cuda()).cpu().numpy().view(np.uint64), want)
         gpu = N.mphf_build(data.cuda(), N.mphf_default_params(hash128=h128, **p), offsets=off.cuda())
         got = u32(N.mphf_query_bytes(gpu, data.cuda(), off.cuda()))
+        assert np.array_equal(u32(N.mphf_query_bytes(gpu, qd.cuda(), qo.cuda())),
+                              oracle_values_of(N, gpu, data=qd, offsets=qo))
     assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
