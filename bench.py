@@ -30,9 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MPHF ns/key & queries/s at n=1e9 u64; % of random-gather roofline; p99 lat"
 UNIT = "queries/s"
-QUERY_KERNEL_SOURCES = ["paper_2502_15539_gb300/csrc/mphf_query.cu", "paper_2502_15539_gb300/csrc/mphf_internal.cuh",
-                        "include/mphf_device.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "query_u64_kernel_n1e9.md")
+QUERY_KERNEL_SOURCES = ["paper_2502_15539_gb300/csrc/mphf_window.cu", "paper_2502_15539_gb300/csrc/mphf_query.cu",
+                        "paper_2502_15539_gb300/csrc/mphf_internal.cuh", "include/mphf_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "query_u64_windowed_n1e9.md")
 
 
 def parse(argv=None):
@@ -94,10 +94,12 @@ def measured_peaks() -> tuple[float, str]:
 
 
 def recorded_traffic(structure_n: int, keys_per_launch: int, l2_fetch_granularity: int = 128):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source, on a structure of the same n and at the same L2
-    fetch granularity; else None.  DRAM bytes per key depend on the structure
-    (its pilot array against L2), not on how many keys one launch queries."""
+    """DRAM bytes of one query step from the committed ncu summary (the sum
+    over the windowed passes of one chunk, per key, times the keys of the
+    step), if it was taken on the current kernel sources, on a structure of
+    the same n and at the same L2 fetch granularity; else None.  DRAM bytes
+    per key depend on the structure (its pilot array against L2) and on the
+    chunk size, not on how many chunks one step queries."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
@@ -202,12 +204,12 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    keys = W.u64_keys(n, seed=0, device=dev)
-    built_here = True
-    if args.structure and os.path.exists(args.structure):
+    built_here = not (args.structure and os.path.exists(args.structure))
+    # A loaded structure with a sampled query needs no full key set on the device.
+    keys = W.u64_keys(n, seed=0, device=dev) if built_here or not 0 < args.query_keys < n else None
+    if not built_here:
         with open(args.structure, "rb") as f:
             m = N.mphf_deserialize(f.read())
-        built_here = False
     else:
         m = N.mphf_build(keys)
         if args.structure:
@@ -274,6 +276,13 @@ def run_gpu(args):
     matched_ms = statistics.mean(time_steps(run_matched, args.steps))
     del bidx
     torch.cuda.empty_cache()
+    # The single-pass kernel on the same stream (one window): the kernel the
+    # matched probe bounds; the windowed path replaces its random DRAM reads.
+    run_single = lambda: N.mphf_query_u64_windowed(m, q, probe_out, window_bytes=1 << 40, stream=stream)
+    for _ in range(args.warmup):
+        run_single()
+    single_ms = statistics.mean(time_steps(run_single, args.steps))
+    single_same = bool(torch.equal(probe_out, out))
     # (b) uniform: one byte at a uniformly random index of a table the size of the pilot array.
     table = torch.randint(0, 256, (info["pilot_bytes"],), dtype=torch.uint8, device=dev)
     run_probe = lambda: N.mphf_gather_probe(q, table, probe_out, stream=stream)
@@ -282,8 +291,12 @@ def run_gpu(args):
     probe_ms = statistics.mean(time_steps(run_probe, args.steps))
     del table, probe_out
 
-    # Roofline of the query kernel (HBM bound): algorithmic bytes per key =
+    # Roofline of the query step (HBM bound): algorithmic bytes per key =
     # 8 (key) + 4 (result) + 32 (the pilot's DRAM sector) + 64 per remapped key.
+    W_passes = -(-info["pilot_bytes"] // (72 << 20)) if mq >= (1 << 24) else 1
+    query_path = ("mphf_query_u64, windowed: window_first_kernel, "
+                  f"{W_passes - 2} x window_mid_kernel, window_last_kernel per chunk of up to 2^28 keys"
+                  if W_passes >= 2 else "mphf_query_u64, single pass: query_u64_kernel")
     peak, peak_kind = measured_peaks()
     alg_bytes = mq * (8 + 4 + 32) + remapped * 64
     kernel_ms = statistics.mean(per_step)
@@ -348,7 +361,8 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "alg_bytes_per_key": alg_bytes / mq,
-                         "kernel": "query_u64_kernel"},
+                         "kernel": query_path,
+                         "basis": "the whole query step (every pass) per 1e9 keys, as the step is timed"},
             "gather_roofline": {
                 "frac": matched_ms / kernel_ms, "probe_ms": matched_ms, "query_ms": kernel_ms,
                 "probe": "mphf_gather_probe_at: the query's own pilot gathers (its bucket indexes for the same "
@@ -356,6 +370,11 @@ def run_gpu(args):
                          "u32 out",
                 "probe_gathers_per_s": mq / (matched_ms / 1e3),
                 "query_pilot_gathers_per_s": mq / (kernel_ms / 1e3),
+                "single_pass": {"query_ms": single_ms, "queries_per_s": mq / (single_ms / 1e3),
+                                "frac": matched_ms / single_ms, "outputs_identical": single_same,
+                                "kernel": "query_u64_kernel (mphf_query_u64_windowed with one window)"},
+                "note": "frac > 1: the windowed query reads each pilot from an L2-resident window, so it is not "
+                        "bound by the random DRAM gathers the probe makes; the probe bounds the single pass",
                 "uniform": {"probe_ms": probe_ms, "frac": probe_ms / kernel_ms,
                             "probe": "mphf_gather_probe: same key stream, 1 byte at a uniformly random index "
                                      f"of a {info['pilot_bytes']}-byte table per key (no skew)"},

@@ -146,7 +146,7 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
  * mphf_query_u64_windowed with its defaults; everything else runs the
  * single-pass kernel.  Both give the same values.  The windowed path's first
  * use on a structure allocates its scratch (cudaMalloc, 6 bytes per key of a
- * chunk of at most 2^27 keys, 805 MB at most), which the structure keeps
+ * chunk of at most 2^28 keys, 1.6 GB at most), which the structure keeps
  * until mphf_free; make that first large query outside stream capture.  If
  * the scratch cannot be allocated, the single-pass kernel runs instead. */
 
@@ -162,7 +162,7 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
  * middle pass.  Results equal mphf_query_u64's, key by key.
  *   window_bytes  pilot bytes per range; 0: 72 MiB.  W = 1 (window_bytes >=
  *                 P B) runs the single-pass kernel.
- *   chunk_keys    keys per chunk (even, at most 2^31; 0: 2^27).  Every chunk
+ *   chunk_keys    keys per chunk (even, at most 2^31; 0: 2^28).  Every chunk
  *                 reads the pilot array once more; the scratch is 6 bytes per
  *                 key of a chunk, owned by the structure (allocated on first
  *                 use, grown when a larger chunk is asked for, freed by

@@ -17,18 +17,25 @@
 //
 // Sequential traffic per key: 13 B in pass 0, 6 B in each middle pass and
 // 17 B in the last, against one random DRAM access in the single pass.
-// Keys are processed in chunks of at most 2^27, so the scratch streams (6 B
-// per key of a chunk, 805 MB) are bounded; every chunk re-reads the pilot
-// windows once (286 MB per 2^27 keys at n = 1e9, about 2 B per key).
+// Keys are processed in chunks of at most 2^28, so the scratch streams (6 B
+// per key of a chunk, 1.6 GB) are bounded; every chunk re-reads the pilot
+// windows once (286 MB per 2^28 keys at n = 1e9, about 1 B per key).
 #include "mphf_internal.cuh"
 
 namespace ptrhash {
 
+// Launch shapes (measured at n = 1e9, one 2^28-key chunk per pass: keys per
+// thread / resident CTAs per SM): the first pass 8 / 5 (0.77 ms; 8 / 4 took
+// 0.81, 4 / 8 0.83), the middle passes 16 / 4 (0.40 ms), the last pass 4 / 8
+// (0.95 ms; 8 / 4 took 1.13, 8 / 5 1.03).  The last pass has the most
+// arithmetic per key and the most streams; more resident warps hide its
+// load latency better than more keys per thread.
 constexpr int kWinThreads = 256;
-constexpr int kWinKeys = 8;       // keys per thread in the first and last pass
-constexpr int kWinMidKeys = 16;   // keys per thread in the middle passes
+constexpr int kWinFirstKeys = 8;    // keys per thread in the first pass
+constexpr int kWinMidKeys = 16;     // keys per thread in the middle passes
+constexpr int kWinLastKeys = 4;     // keys per thread in the last pass
 constexpr uint64_t kWindowBytesDefault = 72ull << 20;
-constexpr uint64_t kWindowChunkDefault = 1ull << 27;
+constexpr uint64_t kWindowChunkDefault = 1ull << 28;
 constexpr uint64_t kWindowMinKeys = 1ull << 24;
 
 // hi and lo of the 128-bit product a b for a < 2^32, from two 32 x 32 -> 64
@@ -54,10 +61,10 @@ __device__ __forceinline__ bool in_window(uint64_t b, uint64_t lo, uint64_t hi) 
 
 // Pass 0: bucket index of every key, and the pilot of the keys in [blo, bhi).
 template <int GAMMA>
-__global__ void __launch_bounds__(kWinThreads, 4)
+__global__ void __launch_bounds__(kWinThreads, 5)
 window_first_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
                     uint32_t *__restrict__ b32, uint8_t *__restrict__ q, const uint64_t blo, const uint64_t bhi) {
-    constexpr int K = kWinKeys;
+    constexpr int K = kWinFirstKeys;
     const uint64_t tile = (uint64_t)blockIdx.x * (kWinThreads * K);
     if (tile + kWinThreads * K > count) {
         for (uint64_t i = tile + threadIdx.x; i < count; i += kWinThreads) {
@@ -124,11 +131,11 @@ window_mid_kernel(const uint8_t *__restrict__ pilots, const uint32_t *__restrict
 // quotient over an integer).  hp(p) = C (p xor seed) comes from a table of
 // the 256 pilot values in shared memory.
 template <int REDUCE, int REMAP>
-__global__ void __launch_bounds__(kWinThreads, 4)
+__global__ void __launch_bounds__(kWinThreads, 8)
 window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
                    const uint32_t *__restrict__ b32, const uint8_t *__restrict__ qin, uint32_t *__restrict__ out,
                    const uint64_t blo, const uint64_t bhi, const uint64_t part_magic) {
-    constexpr int K = kWinKeys;
+    constexpr int K = kWinLastKeys;
     __shared__ uint64_t hp[256];
     hp[threadIdx.x] = v.C * ((uint64_t)threadIdx.x ^ v.seed);   // kWinThreads == 256
     __syncthreads();
@@ -183,17 +190,18 @@ static int run_windows(const View &v, const uint64_t *keys, uint64_t count, uint
     uint8_t *qa = scratch + 4 * chunk, *qb = qa + chunk;
     for (uint64_t c0 = 0; c0 < count; c0 += chunk) {
         const uint64_t cnt = count - c0 < chunk ? count - c0 : chunk;
-        const unsigned blocks = (unsigned)((cnt + kWinThreads * kWinKeys - 1) / (kWinThreads * kWinKeys));
+        const unsigned first_blocks = (unsigned)((cnt + kWinThreads * kWinFirstKeys - 1) / (kWinThreads * kWinFirstKeys));
         const unsigned mid_blocks = (unsigned)((cnt + kWinThreads * kWinMidKeys - 1) / (kWinThreads * kWinMidKeys));
+        const unsigned last_blocks = (unsigned)((cnt + kWinThreads * kWinLastKeys - 1) / (kWinThreads * kWinLastKeys));
         uint8_t *qi = qa, *qo = qb;
         for (uint64_t w = 0; w < W; w++) {
             const uint64_t blo = nbkt * w / W, bhi = nbkt * (w + 1) / W;
             if (w == 0)
-                window_first_kernel<GAMMA><<<blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qo, blo, bhi);
+                window_first_kernel<GAMMA><<<first_blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qo, blo, bhi);
             else if (w + 1 < W)
                 window_mid_kernel<<<mid_blocks, kWinThreads, 0, s>>>(v.pilots, b32, cnt, qi, qo, blo, bhi);
             else
-                window_last_kernel<REDUCE, REMAP><<<blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qi,
+                window_last_kernel<REDUCE, REMAP><<<last_blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qi,
                                                                                out + c0, blo, bhi, part_magic);
             count_launch();
             const cudaError_t e = cudaGetLastError();

@@ -1,7 +1,7 @@
 """The bench's `traffic` figure comes from the committed ncu summary of the
-query kernel.  That record names the sha of the kernel's sources and the L2
-fetch granularity it was captured at; both must match what bench.py runs,
-else the figure would describe a different kernel."""
+query step (the windowed passes of one chunk).  That record names the sha of
+the kernels' sources and the L2 fetch granularity it was captured at; both
+must match what bench.py runs, else the figure would describe other kernels."""
 from __future__ import annotations
 
 import os
@@ -22,4 +22,4 @@ def test_traffic_record_matches_the_current_query_kernel():
 def test_traffic_record_is_refused_at_another_granularity_or_structure():
     assert bench.recorded_traffic(10**9, 10**9, 32) is None
     assert bench.recorded_traffic(10**8, 10**8, 128) is None   # a smaller structure: other bytes per key
-    assert bench.recorded_traffic(10**9, 2**26, 128) == 81.88 * 2**26
+    assert bench.recorded_traffic(10**9, 2**26, 128) == 56.86 * 2**26

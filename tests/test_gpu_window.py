@@ -53,9 +53,9 @@ def test_windowed_query_matches_oracle(n, params, windows):
         assert np.array_equal(got, want), f"W={windows} chunk={chunk}: {int((got != want).sum())} mismatches"
 
 
-@pytest.mark.parametrize("count", [1, 2, 3, 2047, 2048, 2049, 4097, 2 * 4096 + 1])
+@pytest.mark.parametrize("count", [1, 2, 3, 1023, 1025, 2047, 2048, 2049, 4097, 2 * 4096 + 1])
 def test_windowed_query_ragged_counts(count):
-    """Counts below, at and around the 2048- and 4096-key tiles of the passes."""
+    """Counts below, at and around the 1024-, 2048- and 4096-key tiles of the passes."""
     N = need_gpu()
     n = 50_000
     ref, blob = oracle_structure(n, 0, slots_override=4096, alpha=0.9)
