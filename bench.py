@@ -294,6 +294,7 @@ def run_gpu(args):
     # Roofline of the query step (HBM bound): algorithmic bytes per key =
     # 8 (key) + 4 (result) + 32 (the pilot's DRAM sector) + 64 per remapped key.
     W_passes = -(-info["pilot_bytes"] // (72 << 20)) if mq >= (1 << 24) else 1
+    W_passes = W_passes if W_passes <= 8 else 1   # the library's automatic choice
     query_path = ("mphf_query_u64, windowed: window_first_kernel, "
                   f"{W_passes - 2} x window_mid_kernel, window_last_kernel per chunk of up to 2^28 keys"
                   if W_passes >= 2 else "mphf_query_u64, single pass: query_u64_kernel")

@@ -141,10 +141,12 @@ int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
 int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
                    uint32_t *out_dev, void *stream);
 /* How mphf_query_u64 runs: a batch of at least 2^24 keys against a pilot
- * array above 72 MiB (n above about 2.5e8 with the Default parameters), with
- * 16-byte aligned keys and 8-byte aligned out, takes the windowed path of
- * mphf_query_u64_windowed with its defaults; everything else runs the
- * single-pass kernel.  Both give the same values.  The windowed path's first
+ * array above 72 MiB and at most 576 MiB (n from about 2.5e8 to 2e9 with the
+ * Default parameters; the passes then stay fewer than 9), with
+ * 16-byte aligned keys and out aligned to two elements, takes the windowed
+ * path of mphf_query_u64_windowed with its defaults; everything else runs
+ * the single-pass kernel.  Both give the same values.  mphf_query_u64_phf,
+ * mphf_query_u64_wide and mphf_lookup_u64 choose the same way.  The windowed path's first
  * use on a structure allocates its scratch (cudaMalloc, 6 bytes per key of a
  * chunk of at most 2^28 keys, 1.6 GB at most), which the structure keeps
  * until mphf_free; make that first large query outside stream capture.  If
@@ -474,7 +476,10 @@ int mphf_set_l2_fetch_granularity(int bytes, int *previous);
  * Sec. 3.4) and table holds n elements of elem_bytes (4 or 8) bytes.  This is
  * the MPHF's use as the index of a static key set (Sec. 1, Motivation) with
  * the lookup streamed inside the consuming kernel (Sec. 5): one kernel, the
- * value never stored.  Non-member keys read some element of the table.
+ * value never stored (large batches against a pilot array above L2 run the
+ * windowed passes of mphf_query_u64_windowed, whose last pass reads the
+ * table entry instead of writing the value).  Non-member keys read some
+ * element of the table.
  * keys_dev: count u64 (device, 8-byte aligned); table_dev: n elements
  * (device, aligned to elem_bytes; owned by the caller); out_dev: count
  * elements (device, aligned to elem_bytes).  Any n, including n > 2^32.

@@ -431,10 +431,15 @@ static int check_query_u64(const mphf_t *m, const uint64_t *keys_dev, const uint
     return MPHF_OK;
 }
 
+}  // extern "C"
+
+namespace ptrhash {
+
 // The windowed query on the handle's scratch.  Returns MPHF_ERR_OOM (and
 // leaves no CUDA error pending) if the scratch cannot be allocated.
-static int windowed_query(mphf_t *m, const uint64_t *keys, uint64_t count, uint32_t *out, uint64_t W,
-                          uint64_t chunk_keys, cudaStream_t s) {
+int handle_windowed_query(const mphf_t *mc, const uint64_t *keys, uint64_t count, void *out, int mode,
+                          const void *table, uint64_t W, uint64_t chunk_keys, cudaStream_t s) {
+    mphf_t *m = const_cast<mphf_t *>(mc);   // the scratch is mutable state of a const structure
     const uint64_t chunk = window_chunk_for(count, chunk_keys);
     std::lock_guard<std::mutex> lock(m->win_mu);
     if (m->win_chunk < chunk) {
@@ -459,11 +464,27 @@ static int windowed_query(mphf_t *m, const uint64_t *keys, uint64_t count, uint3
     cudaError_t e = cudaStreamWaitEvent(s, m->win_done, 0);
     if (e != cudaSuccess) return cuda_fail(e, "windowed query: order after the previous use");
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
-    const int rc = launch_query_u64_windowed(m->hdr, v, keys, count, out, W, chunk, m->d_win, s);
+    const int rc = launch_query_u64_windowed(m->hdr, v, keys, count, out, mode, table, W, chunk, m->d_win, s);
     e = cudaEventRecord(m->win_done, s);
     if (rc == MPHF_OK && e != cudaSuccess) return cuda_fail(e, "windowed query: record");
     return rc;
 }
+
+// The automatic choice of the query entry points: the windowed path for a
+// large batch against a pilot array above the window size, with buffers
+// aligned for it.  Returns 1 if it ran (rc holds its result), 0 if the
+// single pass should run (not applicable, or no room for the scratch).
+int try_windowed(const mphf_t *m, const uint64_t *keys, uint64_t count, void *out, int mode, const void *table,
+                 cudaStream_t s, int *rc) {
+    const uint64_t W = window_plan(m->hdr, count);
+    if (W < 2 || !window_supported(m->hdr, keys, out, window_out_bytes(mode))) return 0;
+    *rc = handle_windowed_query(m, keys, count, out, mode, table, W, 0, s);
+    return *rc != MPHF_ERR_OOM;
+}
+
+}  // namespace ptrhash
+
+extern "C" {
 
 int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint32_t *out_dev,
                    void *stream) {
@@ -471,11 +492,8 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, ui
     if (count == 0) return MPHF_OK;
     int rc = check_query_u64(m, keys_dev, out_dev);
     if (rc) return rc;
-    const uint64_t W = window_plan(m->hdr, count);
-    if (W >= 2 && window_supported(m->hdr, keys_dev, out_dev)) {
-        rc = windowed_query(const_cast<mphf_t *>(m), keys_dev, count, out_dev, W, 0, (cudaStream_t)stream);
-        if (rc != MPHF_ERR_OOM) return rc;   // no room for the scratch: the single pass needs none
-    }
+    // No room for the windowed path's scratch: the single pass needs none.
+    if (try_windowed(m, keys_dev, count, out_dev, kWinMphf32, nullptr, (cudaStream_t)stream, &rc)) return rc;
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
     return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, false, (cudaStream_t)stream);
 }
@@ -495,11 +513,11 @@ int mphf_query_u64_windowed(const mphf_t *m, const uint64_t *keys_dev, uint64_t 
         View v = make_view(m->hdr, m->d_pilots, m->d_remap);
         return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, false, (cudaStream_t)stream);
     }
-    if (!window_supported(m->hdr, keys_dev, out_dev)) {
+    if (!window_supported(m->hdr, keys_dev, out_dev, 4)) {
         set_error("windowed query: keys 16-byte and out 8-byte aligned, P B < 2^32");
         return MPHF_ERR_ARG;
     }
-    return windowed_query(const_cast<mphf_t *>(m), keys_dev, count, out_dev, W, chunk_keys, (cudaStream_t)stream);
+    return handle_windowed_query(m, keys_dev, count, out_dev, kWinMphf32, nullptr, W, chunk_keys, (cudaStream_t)stream);
 }
 
 int mphf_bucket_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count, uint64_t *out_dev, void *stream) {
@@ -527,6 +545,8 @@ int mphf_query_u64_wide(const mphf_t *m, const uint64_t *keys_dev, uint64_t coun
         return MPHF_ERR_ARG;
     }
     if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
+    int rc = MPHF_OK;
+    if (try_windowed(m, keys_dev, count, out_dev, kWinWide64, nullptr, (cudaStream_t)stream, &rc)) return rc;
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
     return launch_query_u64_wide(m->hdr, v, keys_dev, count, out_dev, (cudaStream_t)stream);
 }
@@ -541,6 +561,8 @@ int mphf_query_u64_phf(const mphf_t *m, const uint64_t *keys_dev, uint64_t count
     }
     if (m->hdr.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
     if (m->hdr.P * m->hdr.S > (1ull << 32)) { set_error("P S > 2^32: slots do not fit 32 bits"); return MPHF_ERR_ARG; }
+    int rc = MPHF_OK;
+    if (try_windowed(m, keys_dev, count, out_dev, kWinPhf32, nullptr, (cudaStream_t)stream, &rc)) return rc;
     View v = make_view(m->hdr, m->d_pilots, m->d_remap);
     return launch_query_u64(m->hdr, v, keys_dev, count, out_dev, true, (cudaStream_t)stream);
 }

@@ -72,12 +72,29 @@ int launch_query_bytes_wide(const Header &h, const View &v, const uint8_t *bytes
 // Windowed query (mphf_window.cu): the pilot array in W byte ranges that stay
 // L2-resident, the keys streamed once per range.  window_plan gives the W the
 // automatic path uses for a structure and batch size (1: single pass).
+// The output forms: u32 MPHF values, u32 slots (PHF), u64 values, and the
+// fused lookup out[i] = table[value] with 4- or 8-byte elements.
+enum : int { kWinMphf32 = 0, kWinPhf32 = 1, kWinWide64 = 2, kWinTable4 = 3, kWinTable8 = 4 };
 uint64_t window_count_for(uint64_t nbkt, uint64_t window_bytes);
 uint64_t window_plan(const Header &h, uint64_t count);
 uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys);
-bool window_supported(const Header &h, const uint64_t *keys, const uint32_t *out);
-int launch_query_u64_windowed(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint32_t *out,
-                              uint64_t W, uint64_t chunk, uint8_t *scratch, cudaStream_t s);
+int window_out_bytes(int mode);
+// Keys 16-byte aligned, out aligned to two elements, P B < 2^32.
+bool window_supported(const Header &h, const uint64_t *keys, const void *out, int out_bytes);
+int launch_query_u64_windowed(const Header &h, const View &v, const uint64_t *keys, uint64_t count, void *out,
+                              int mode, const void *table, uint64_t W, uint64_t chunk, uint8_t *scratch,
+                              cudaStream_t s);
+// The windowed query on a structure's own scratch (mphf_api.cu): W >= 2
+// windows, chunk_keys 0 for the default.  MPHF_ERR_OOM (no CUDA error left
+// pending) if the scratch cannot be allocated.
+int handle_windowed_query(const mphf *m, const uint64_t *keys, uint64_t count, void *out, int mode,
+                          const void *table, uint64_t W, uint64_t chunk_keys, cudaStream_t s);
+// The automatic choice of the query entry points: runs the windowed path and
+// returns 1 (its result in *rc) for a batch of at least 2^24 keys against a
+// pilot array of 2 to 8 windows of 72 MiB with aligned buffers; else returns 0 and the
+// caller runs the single pass (also when the scratch cannot be allocated).
+int try_windowed(const mphf *m, const uint64_t *keys, uint64_t count, void *out, int mode, const void *table,
+                 cudaStream_t s, int *rc);
 
 // Global bucket index of each u64 key (mphf_query.cu).
 int launch_bucket_u64(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint64_t *out,

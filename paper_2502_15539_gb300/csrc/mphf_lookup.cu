@@ -7,9 +7,12 @@
 // value never leaves registers, so the separate query pass's 4-byte write and
 // the gather pass's 4-byte re-read per key disappear, and so does a launch.
 //
-// The kernel is written against the public device API (mphf_device.cuh),
-// exactly as an application kernel would use it: eval_u64_n puts K pilot
-// gathers in flight per thread, then the K table reads go out together.
+// The single-pass kernel is written against the public device API
+// (mphf_device.cuh), exactly as an application kernel would use it:
+// eval_u64_n puts K pilot gathers in flight per thread, then the K table
+// reads go out together.  Large batches against a pilot array above L2 take
+// the windowed query instead (mphf_window.cu), whose last pass does the
+// table read.
 // Table reads are evict-first (ld.global.cs): each touches a line of a table
 // far larger than L2 once, and with the default policy those lines displace
 // pilot lines (at 1e9 keys and a 4 GB table, 36.6 ms instead of 33.8 ms).
@@ -95,6 +98,10 @@ extern "C" int mphf_lookup_u64(const mphf_t *m, const uint64_t *keys_dev, uint64
     if (rc) return rc;
     if (v.key_kind != MPHF_KEY_U64) { set_error("structure was built for byte keys"); return MPHF_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
+    // Large batches against a pilot array above L2 take the windowed query,
+    // whose last pass reads the table entry in place of writing the value.
+    if (try_windowed(m, keys_dev, count, out_dev, elem_bytes == 4 ? kWinTable4 : kWinTable8, table_dev, s, &rc))
+        return rc;
     return elem_bytes == 4 ? launch_lookup<unsigned int>(v, keys_dev, count, table_dev, out_dev, s)
                            : launch_lookup<unsigned long long>(v, keys_dev, count, table_dev, out_dev, s);
 }

@@ -125,34 +125,60 @@ window_mid_kernel(const uint8_t *__restrict__ pilots, const uint32_t *__restrict
     }
 }
 
-// Last pass: the MPHF value of every key (Eq. slot, Sec. 3.4 remap).  The
-// part is b / B, taken as hi(b M) with M = ceil(2^64 / B), exact for b, B <
-// 2^32 (the error b (M - 2^64 / B) / 2^64 < 2^-32 < 1 / B cannot carry the
-// quotient over an integer).  hp(p) = C (p xor seed) comes from a table of
-// the 256 pilot values in shared memory.
-template <int REDUCE, int REMAP>
+// Last pass: the value of every key (Eq. slot, Sec. 3.4 remap), written in
+// one of the output forms below.  The part is b / B, taken as hi(b M) with
+// M = ceil(2^64 / B), exact for b, B < 2^32 (the error b (M - 2^64 / B) /
+// 2^64 < 2^-32 < 1 / B cannot carry the quotient over an integer).
+// hp(p) = C (p xor seed) comes from a table of the 256 pilot values in
+// shared memory.
+//   kOutMphf32  u32 MPHF values (n <= 2^32)
+//   kOutPhf32   u32 slots, no remap (P S <= 2^32)
+//   kOutWide64  u64 MPHF values (any n)
+//   kOutTable4 / kOutTable8  out[i] = table[value]: the fused lookup, with
+//               4- or 8-byte table elements; the table is read evict-first
+//               (each read touches a line of a table far larger than L2 once,
+//               and would otherwise displace the pilot window's lines)
+enum : int { kOutMphf32 = 0, kOutPhf32 = 1, kOutWide64 = 2, kOutTable4 = 3, kOutTable8 = 4 };
+
+template <int OUT> struct WindowOut { using T = uint32_t; };
+template <> struct WindowOut<kOutWide64> { using T = unsigned long long; };
+template <> struct WindowOut<kOutTable8> { using T = unsigned long long; };
+
+template <int REDUCE, int REMAP, int OUT>
 __global__ void __launch_bounds__(kWinThreads, 8)
 window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
-                   const uint32_t *__restrict__ b32, const uint8_t *__restrict__ qin, uint32_t *__restrict__ out,
-                   const uint64_t blo, const uint64_t bhi, const uint64_t part_magic) {
+                   const uint32_t *__restrict__ b32, const uint8_t *__restrict__ qin,
+                   typename WindowOut<OUT>::T *__restrict__ out, const uint64_t blo, const uint64_t bhi,
+                   const uint64_t part_magic, const typename WindowOut<OUT>::T *__restrict__ table) {
+    using T = typename WindowOut<OUT>::T;
+    constexpr bool kWideValue = OUT == kOutWide64 || OUT == kOutTable4 || OUT == kOutTable8;
     constexpr int K = kWinLastKeys;
     __shared__ uint64_t hp[256];
     hp[threadIdx.x] = v.C * ((uint64_t)threadIdx.x ^ v.seed);   // kWinThreads == 256
     __syncthreads();
-    auto value = [&](uint64_t key, uint32_t b, uint32_t pilot) -> uint32_t {
+    auto value = [&](uint64_t key, uint32_t b, uint32_t pilot) -> uint64_t {
         uint64_t unused;
         const uint64_t part = v.B == 1 ? b : hi32x64(b, part_magic, unused);
         const uint64_t s = part * v.S + reduce_slot<REDUCE>(v, (v.C * key) ^ hp[pilot]);
-        if (s < v.n) return (uint32_t)s;
-        const uint32_t j = (uint32_t)(s - v.n);
-        if constexpr (REMAP == kRemapClef) return clef_get(static_cast<const uint8_t *>(v.remap), j);
-        else return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+        if (OUT == kOutPhf32 || s < v.n) return s;
+        const uint64_t j = s - v.n;
+        if constexpr (REMAP == kRemapClef) {
+            if constexpr (kWideValue) return clef_get64(static_cast<const uint8_t *>(v.remap), j);
+            else return clef_get(static_cast<const uint8_t *>(v.remap), (uint32_t)j);
+        } else {
+            if (kWideValue && v.n > (1ull << 32)) return __ldg(static_cast<const unsigned long long *>(v.remap) + j);
+            return __ldg(static_cast<const uint32_t *>(v.remap) + j);
+        }
+    };
+    auto emit = [&](uint64_t val) -> T {
+        if constexpr (OUT == kOutTable4 || OUT == kOutTable8) return __ldcs(table + val);
+        else return (T)val;
     };
     const uint64_t tile = (uint64_t)blockIdx.x * (kWinThreads * K);
     if (tile + kWinThreads * K > count) {
         for (uint64_t i = tile + threadIdx.x; i < count; i += kWinThreads) {
             const uint32_t b = b32[i];
-            out[i] = value(__ldcs(keys + i), b, in_window(b, blo, bhi) ? __ldg(v.pilots + b) : qin[i]);
+            out[i] = emit(value(__ldcs(keys + i), b, in_window(b, blo, bhi) ? __ldg(v.pilots + b) : qin[i]));
         }
         return;
     }
@@ -172,19 +198,25 @@ window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64
 #pragma unroll
     for (int q = 0; q < K; q++)
         p[q] = in_window(b[q], blo, bhi) ? (uint32_t)__ldg(v.pilots + b[q]) : (c[q >> 1] >> (8 * (q & 1))) & 0xFFu;
+    T r[K];
+#pragma unroll
+    for (int q = 0; q < K; q++) r[q] = emit(value(k[q], b[q], p[q]));
 #pragma unroll
     for (int j = 0; j < K / 2; j++) {
         const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
-        __stcs(reinterpret_cast<uint2 *>(out + i),
-               make_uint2(value(k[2 * j], b[2 * j], p[2 * j]), value(k[2 * j + 1], b[2 * j + 1], p[2 * j + 1])));
+        if constexpr (sizeof(T) == 4) __stcs(reinterpret_cast<uint2 *>(out + i), make_uint2(r[2 * j], r[2 * j + 1]));
+        else __stcs(reinterpret_cast<ulonglong2 *>(out + i), make_ulonglong2(r[2 * j], r[2 * j + 1]));
     }
 }
 
 static_assert(kWinThreads == 256, "the last pass fills its 256-entry hp table with one thread per pilot value");
 
-template <int GAMMA, int REDUCE, int REMAP>
-static int run_windows(const View &v, const uint64_t *keys, uint64_t count, uint32_t *out, uint64_t W,
-                       uint64_t chunk, uint64_t part_magic, uint8_t *scratch, cudaStream_t s) {
+template <int GAMMA, int REDUCE, int REMAP, int OUT>
+static int run_windows(const View &v, const uint64_t *keys, uint64_t count, void *out_v, const void *table_v,
+                       uint64_t W, uint64_t chunk, uint64_t part_magic, uint8_t *scratch, cudaStream_t s) {
+    using T = typename WindowOut<OUT>::T;
+    T *out = static_cast<T *>(out_v);
+    const T *table = static_cast<const T *>(table_v);
     const uint64_t nbkt = v.P * v.B;
     uint32_t *b32 = reinterpret_cast<uint32_t *>(scratch);
     uint8_t *qa = scratch + 4 * chunk, *qb = qa + chunk;
@@ -201,8 +233,8 @@ static int run_windows(const View &v, const uint64_t *keys, uint64_t count, uint
             else if (w + 1 < W)
                 window_mid_kernel<<<mid_blocks, kWinThreads, 0, s>>>(v.pilots, b32, cnt, qi, qo, blo, bhi);
             else
-                window_last_kernel<REDUCE, REMAP><<<last_blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qi,
-                                                                               out + c0, blo, bhi, part_magic);
+                window_last_kernel<REDUCE, REMAP, OUT><<<last_blocks, kWinThreads, 0, s>>>(
+                    v, keys + c0, cnt, b32, qi, out + c0, blo, bhi, part_magic, table);
             count_launch();
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(e, "windowed query launch");
@@ -219,9 +251,15 @@ uint64_t window_count_for(uint64_t nbkt, uint64_t window_bytes) {
     return (nbkt + window_bytes - 1) / window_bytes;
 }
 
+// Every middle pass streams 6 bytes per key, so past about 8 windows the
+// passes cost more than the random DRAM reads they replace: at n = 4.5e9
+// (1.29 GB of pilots, 18 windows) the windowed path took 112 ms per 4.5e9 keys
+// against 82.8 ms for the single pass, at n = 1e9 (4 windows) 9.4 against 12.5.
+constexpr uint64_t kWindowMaxAuto = 8;
+
 uint64_t window_plan(const Header &h, uint64_t count) {
     const uint64_t W = window_count_for(h.P * h.B, 0);
-    return (W >= 2 && count >= kWindowMinKeys) ? W : 1;
+    return (W >= 2 && W <= kWindowMaxAuto && count >= kWindowMinKeys) ? W : 1;
 }
 
 uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys) {
@@ -230,38 +268,59 @@ uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys) {
     return chunk < even ? chunk : even;
 }
 
-bool window_supported(const Header &h, const uint64_t *keys, const uint32_t *out) {
+bool window_supported(const Header &h, const uint64_t *keys, const void *out, int out_bytes) {
     const uint64_t nbkt = h.P * h.B;
     return h.B > 0 && h.P < (1ull << 32) && h.B < (1ull << 32) && nbkt < (1ull << 32) && ((uintptr_t)keys % 16) == 0 &&
-           ((uintptr_t)out % 8) == 0;
+           ((uintptr_t)out % (2 * out_bytes)) == 0;
 }
 
-template <int GAMMA, int REDUCE>
-static int run_windows_remap(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint32_t *out,
-                             uint64_t W, uint64_t chunk, uint64_t part_magic, uint8_t *scratch, cudaStream_t s) {
+template <int GAMMA, int REDUCE, int OUT>
+static int run_windows_remap(const Header &h, const View &v, const uint64_t *keys, uint64_t count, void *out,
+                             const void *table, uint64_t W, uint64_t chunk, uint64_t part_magic, uint8_t *scratch,
+                             cudaStream_t s) {
+    if (OUT == kOutPhf32)
+        return run_windows<GAMMA, REDUCE, kRemapNone, OUT>(v, keys, count, out, table, W, chunk, part_magic, scratch, s);
     if (h.remap == MPHF_REMAP_VEC)
-        return run_windows<GAMMA, REDUCE, kRemapVec>(v, keys, count, out, W, chunk, part_magic, scratch, s);
-    return run_windows<GAMMA, REDUCE, kRemapClef>(v, keys, count, out, W, chunk, part_magic, scratch, s);
+        return run_windows<GAMMA, REDUCE, kRemapVec, OUT>(v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+    return run_windows<GAMMA, REDUCE, kRemapClef, OUT>(v, keys, count, out, table, W, chunk, part_magic, scratch, s);
 }
+
+template <int OUT>
+static int run_windows_layout(const Header &h, const View &v, const uint64_t *keys, uint64_t count, void *out,
+                              const void *table, uint64_t W, uint64_t chunk, uint64_t part_magic, uint8_t *scratch,
+                              cudaStream_t s) {
+    const bool cubic = h.gamma == MPHF_GAMMA_CUBIC, pow2 = h.reduce == kReducePow2;
+    if (cubic && pow2)
+        return run_windows_remap<MPHF_GAMMA_CUBIC, kReducePow2, OUT>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+    if (cubic)
+        return run_windows_remap<MPHF_GAMMA_CUBIC, kReduceMod, OUT>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+    if (pow2)
+        return run_windows_remap<MPHF_GAMMA_LINEAR, kReducePow2, OUT>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+    return run_windows_remap<MPHF_GAMMA_LINEAR, kReduceMod, OUT>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+}
+
+int window_out_bytes(int mode) { return mode == kWinWide64 || mode == kWinTable8 ? 8 : 4; }
 
 // scratch: 6 chunk bytes of device memory (the bucket stream and two
 // carried-pilot streams of one chunk), at least 8-byte aligned.
-int launch_query_u64_windowed(const Header &h, const View &v, const uint64_t *keys, uint64_t count, uint32_t *out,
-                              uint64_t W, uint64_t chunk, uint8_t *scratch, cudaStream_t s) {
-    if (W < 2 || chunk < 2 || chunk % 2 || chunk > (1ull << 31) || !window_supported(h, keys, out)) {
+int launch_query_u64_windowed(const Header &h, const View &v, const uint64_t *keys, uint64_t count, void *out,
+                              int mode, const void *table, uint64_t W, uint64_t chunk, uint8_t *scratch,
+                              cudaStream_t s) {
+    if (W < 2 || chunk < 2 || chunk % 2 || chunk > (1ull << 31) ||
+        !window_supported(h, keys, out, window_out_bytes(mode))) {
         set_error("windowed query: W >= 2, an even chunk of at most 2^31 keys, P B < 2^32, aligned buffers");
         return MPHF_ERR_ARG;
     }
     // M = ceil(2^64 / B) gives the part of a bucket index (B >= 2).
     const uint64_t part_magic = h.B == 1 ? 0 : (uint64_t)((((unsigned __int128)1 << 64) + h.B - 1) / h.B);
-    const bool cubic = h.gamma == MPHF_GAMMA_CUBIC, pow2 = h.reduce == kReducePow2;
-    if (cubic && pow2)
-        return run_windows_remap<MPHF_GAMMA_CUBIC, kReducePow2>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
-    if (cubic)
-        return run_windows_remap<MPHF_GAMMA_CUBIC, kReduceMod>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
-    if (pow2)
-        return run_windows_remap<MPHF_GAMMA_LINEAR, kReducePow2>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
-    return run_windows_remap<MPHF_GAMMA_LINEAR, kReduceMod>(h, v, keys, count, out, W, chunk, part_magic, scratch, s);
+    switch (mode) {
+        case kWinMphf32: return run_windows_layout<kOutMphf32>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+        case kWinPhf32: return run_windows_layout<kOutPhf32>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+        case kWinWide64: return run_windows_layout<kOutWide64>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+        case kWinTable4: return run_windows_layout<kOutTable4>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+        case kWinTable8: return run_windows_layout<kOutTable8>(h, v, keys, count, out, table, W, chunk, part_magic, scratch, s);
+        default: set_error("windowed query: unknown output form"); return MPHF_ERR_ARG;
+    }
 }
 
 }  // namespace ptrhash

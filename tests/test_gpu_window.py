@@ -138,3 +138,35 @@ def test_automatic_path_matches_oracle_on_a_large_batch():
     idx = W.uniform_index(200_000, q.numel(), 3).cuda()
     ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
     assert np.array_equal(u32(auto[idx]), ref.query_u64(W.as_uint64_numpy(q[idx]), threads=16))
+
+
+def test_phf_wide_and_lookup_take_the_windowed_path_with_the_same_values():
+    """The PHF query (slots), the 64-bit query and the fused lookup choose the
+    windowed path like mphf_query_u64: on a 3e8-key structure and a 2^25-key
+    batch each must equal its single-pass result and the oracle."""
+    N = need_gpu()
+    n = 3 * 10**8
+    keys = W.u64_keys(n, 13, device="cuda")
+    m = N.mphf_build(keys, N.mphf_default_params(remap=O.REMAP_VEC))
+    q = torch.cat([keys[:(1 << 25) - 1000], W.nonmember_u64_keys(1000, n, 13, device="cuda")]).contiguous()
+    del keys
+    torch.cuda.empty_cache()
+    ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
+    idx = torch.cat([W.uniform_index(100_000, q.numel(), 4), torch.arange(q.numel() - 1000, q.numel())]).cuda()
+    qs = W.as_uint64_numpy(q[idx])
+    want_vals = ref.query_u64(qs, threads=16)
+    # 64-bit values (windowed: 16-byte aligned output)
+    wide = N.mphf_query_u64_wide(m, q)
+    assert np.array_equal(wide[idx].cpu().numpy().view(np.uint64), want_vals.astype(np.uint64))
+    assert torch.equal(wide.to(torch.int32), N.mphf_query_u64_windowed(m, q, window_bytes=1 << 40))
+    # slots without the remap
+    phf = N.mphf_query_u64_phf(m, q)
+    assert np.array_equal(u32(phf[idx]), ref.slots_u64(qs).astype(np.uint32))
+    # fused lookup, 4- and 8-byte tables whose entry j names j
+    for dtype in (torch.int32, torch.int64):
+        table = torch.arange(n, dtype=dtype, device="cuda") ^ 0x5A5A5A5A
+        got = N.mphf_lookup_u64(m, q, table)
+        assert torch.equal(got, table[wide])
+        del table, got
+        torch.cuda.empty_cache()
+
