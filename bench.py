@@ -523,7 +523,11 @@ def run_fused(args, m, q, idx, stream, time_steps, remapped):
     # 8 (key) + 4 (result) + 32 (pilot sector) + 32 (table sector) + 64 per remapped key.
     alg = mq * (8 + 4 + 32 + 32) + remapped * 64
     del table, fused_out, two_out
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (one_ms / 1e3) / 1e9
     return {"workload": f"out[i] = table[h(q[i])]: {n}-entry u32 table, the main query stream ({mq} keys)",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "alg_bytes_per_key": alg / mq},
             "fused_ms": one_ms, "fused_queries_per_s": mq / (one_ms / 1e3),
             "two_pass_ms": two_ms, "speedup": two_ms / one_ms, "outputs_identical": same,
             "fused_alg_bytes_per_key": alg / mq, "fused_achieved_gbs": alg / (one_ms / 1e3) / 1e9,
@@ -543,14 +547,26 @@ def run_variants(args, m, q, out, stream, time_steps):
         return statistics.mean(time_steps(fn, args.steps))
 
     mq = q.numel()
+    peak, peak_kind = measured_peaks()
+
+    def roofline(alg_per_key, ms_):
+        achieved = alg_per_key * mq / (ms_ / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind, "alg_bytes_per_key": alg_per_key}
+
     ms = timed(lambda: N.mphf_query_u64_phf(m, q, out, stream=stream))
-    res = {"default_phf": {"query_ms": ms, "queries_per_s": mq / (ms / 1e3)}}
+    # PHF: 8 (key) + 4 (slot) + 32 (pilot sector), no remap read.
+    res = {"default_phf": {"query_ms": ms, "queries_per_s": mq / (ms / 1e3), "roofline": roofline(44.0, ms)}}
     for name, prm in (("fast", {"lam": 3.0, "gamma": 1, "remap": 1}), ("compact", {"lam": 4.0})):
         mv = N.mphf_build(q, N.mphf_default_params(**prm))
         info = N.mphf_info(mv)
         ms = timed(lambda: N.mphf_query_u64(mv, q, out, stream=stream))
+        # 8 + 4 + 32 per key, plus one remap sector (32 B Vec entry or 64 B CacheLineEF line) for the
+        # remapped fraction (P S - n) / (P S) of the keys.
+        frac_remap = (info["P"] * info["S"] - info["n"]) / (info["P"] * info["S"])
+        alg = 44.0 + frac_remap * (32.0 if info["remap"] == 1 else 64.0)
         res[name] = {"params": prm, "query_ms": ms, "queries_per_s": mq / (ms / 1e3),
-                     "bits_per_key": info["bits_per_key"], "build_ms": info["build_ms"]}
+                     "bits_per_key": info["bits_per_key"], "build_ms": info["build_ms"], "roofline": roofline(alg, ms)}
         del mv
     return res
 
@@ -588,7 +604,13 @@ def run_wide(args, dev, stream):
         bijective = int(seen.sum(dtype=torch.int64).item()) == n
         del seen
     del out, m
+    # 8 (key) + 8 (value) + 32 (pilot sector) + a 64-byte CacheLineEF line for the remapped keys.
+    peak, peak_kind = measured_peaks()
+    alg = 48.0 + 64.0 * (info["P"] * info["S"] - n) / (info["P"] * info["S"])
+    achieved = alg * n / (ms / 1e3) / 1e9
     return {"workload": f"{n} distinct u64 keys (> 2^32), query all in key order, 64-bit results",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "alg_bytes_per_key": alg},
             "P": info["P"], "S": info["S"], "bits_per_key": info["bits_per_key"],
             "build_ms": info["build_ms"], "build_ns_per_key": 1e6 * info["build_ms"] / n,
             "query_ms": ms, "queries_per_s": n / (ms / 1e3), "output_bijective": bijective}
