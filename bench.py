@@ -293,8 +293,11 @@ def run_gpu(args):
 
     # Roofline of the query step (HBM bound): algorithmic bytes per key =
     # 8 (key) + 4 (result) + 32 (the pilot's DRAM sector) + 64 per remapped key.
-    W_passes = -(-info["pilot_bytes"] // (72 << 20)) if mq >= (1 << 24) else 1
-    W_passes = W_passes if W_passes <= 8 else 1   # the library's automatic choice
+    # The library's automatic window count: ceil(pilot bytes / 100 MB), at
+    # least 2, above 72 MiB of pilots and up to 6 windows, for >= 2^24 keys.
+    pb = info["pilot_bytes"]
+    W_passes = max(2, -(-pb // 100_000_000)) if pb > (72 << 20) and mq >= (1 << 24) else 1
+    W_passes = W_passes if W_passes <= 6 else 1
     query_path = ("mphf_query_u64, windowed: window_first_kernel, "
                   f"{W_passes - 2} x window_mid_kernel, window_last_kernel per chunk of up to 2^28 keys"
                   if W_passes >= 2 else "mphf_query_u64, single pass: query_u64_kernel")
@@ -406,8 +409,9 @@ def run_c1(args, dev, stream, with_oracle: bool):
     """The plain configuration: n = 1e6 distinct u64 keys (seed 0), Default
     parameters, GPU-built structure; all n keys queried once in a seeded
     random order (seed 1).  The query kernel alone, 20 launches, best and
-    median, each timed with CUDA events, both with L2 flushed before every
-    launch (a 256 MB write) and back to back (inputs and structure L2-warm);
+    median, each timed with CUDA events and no host submission gap, both with
+    L2 flushed before every launch (a 256 MB write) and back to back (inputs
+    and structure L2-warm);
     host to host through mphf_query_u64_host with page-locked buffers; and
     two L2-regime gather probes over the same key stream as denominators:
     uniform over a table the size of the pilot array, and the query's own
@@ -429,19 +433,23 @@ def run_c1(args, dev, stream, with_oracle: bool):
     reps = 20
 
     def launches(fn, cold: bool) -> list[float]:
+        """Per-launch device times of `reps` launches.  The GPU first runs a
+        bounded sleep kernel (torch.cuda._sleep, about 4 ms) while the host
+        enqueues every launch, so the launches run back to back and no
+        interval includes host submission time."""
         for _ in range(5):
             fn()
-        ts = []
-        for _ in range(reps):
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda._sleep(8_000_000)
+        for a, b in evs:
             if cold:
                 flush.fill_(1)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             fn()
             b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-        return ts
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
 
     def summary(ts: list[float]) -> dict:
         return {"best_ms": min(ts), "median_ms": statistics.median(ts),

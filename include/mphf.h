@@ -141,16 +141,17 @@ int mphf_build(const mphf_params *params, int key_kind, const void *keys_dev,
 int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
                    uint32_t *out_dev, void *stream);
 /* How mphf_query_u64 runs: a batch of at least 2^24 keys against a pilot
- * array above 72 MiB and at most 576 MiB (n from about 2.5e8 to 2e9 with the
- * Default parameters; the passes then stay fewer than 9), with
- * 16-byte aligned keys and out aligned to two elements, takes the windowed
- * path of mphf_query_u64_windowed with its defaults; everything else runs
- * the single-pass kernel.  Both give the same values.  mphf_query_u64_phf,
- * mphf_query_u64_wide and mphf_lookup_u64 choose the same way.  The windowed path's first
- * use on a structure allocates its scratch (cudaMalloc, 6 bytes per key of a
- * chunk of at most 2^28 keys, 1.6 GB at most), which the structure keeps
- * until mphf_free; make that first large query outside stream capture.  If
- * the scratch cannot be allocated, the single-pass kernel runs instead. */
+ * array above 72 MiB, with 16-byte aligned keys and out aligned to two
+ * elements, takes the windowed path of mphf_query_u64_windowed in W =
+ * ceil(pilot bytes / 100 MB) windows (at least 2), as long as W is at most 6
+ * (pilot arrays up to 600 MB: n from about 2.6e8 to 2.1e9 with the Default
+ * parameters); everything else runs the single-pass kernel.  Both
+ * give the same values.  mphf_query_u64_phf, mphf_query_u64_wide and
+ * mphf_lookup_u64 choose the same way.  The windowed path's first use on a
+ * structure allocates its scratch (cudaMalloc, 6 bytes per key of a chunk of
+ * at most 2^28 keys, 1.6 GB at most), which the structure keeps until
+ * mphf_free; make that first large query outside stream capture.  If the
+ * scratch cannot be allocated, the single-pass kernel runs instead. */
 
 /* The windowed evaluation of the same function (no paper counterpart; the
  * paper's query reads each key's pilot where it lies, Sec. 3.1).  The pilot
@@ -162,8 +163,9 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
  * Sec. 3.4).  Random DRAM reads of the pilot array become L2 hits, at the
  * cost of reading the keys twice and 6 bytes of scratch traffic per key and
  * middle pass.  Results equal mphf_query_u64's, key by key.
- *   window_bytes  pilot bytes per range; 0: 72 MiB.  W = 1 (window_bytes >=
- *                 P B) runs the single-pass kernel.
+ *   window_bytes  pilot bytes per range; 0: the automatic W above (which
+ *                 may be 1).  W = 1 (window_bytes >= P B) runs the
+ *                 single-pass kernel.
  *   chunk_keys    keys per chunk (even, at most 2^31; 0: 2^28).  Every chunk
  *                 reads the pilot array once more; the scratch is 6 bytes per
  *                 key of a chunk, owned by the structure (allocated on first

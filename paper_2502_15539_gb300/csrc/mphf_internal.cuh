@@ -70,8 +70,9 @@ int launch_query_bytes_wide(const Header &h, const View &v, const uint8_t *bytes
                             uint64_t count, uint64_t *out, cudaStream_t s);
 
 // Windowed query (mphf_window.cu): the pilot array in W byte ranges that stay
-// L2-resident, the keys streamed once per range.  window_plan gives the W the
-// automatic path uses for a structure and batch size (1: single pass).
+// L2-resident, the keys streamed once per range.  window_count_for gives W
+// for a window size (0: the automatic count for the pilot array, 1 meaning
+// the single pass); window_plan the W the automatic path uses for a batch.
 // The output forms: u32 MPHF values, u32 slots (PHF), u64 values, and the
 // fused lookup out[i] = table[value] with 4- or 8-byte elements.
 enum : int { kWinMphf32 = 0, kWinPhf32 = 1, kWinWide64 = 2, kWinTable4 = 3, kWinTable8 = 4 };
@@ -91,7 +92,7 @@ int handle_windowed_query(const mphf *m, const uint64_t *keys, uint64_t count, v
                           const void *table, uint64_t W, uint64_t chunk_keys, cudaStream_t s);
 // The automatic choice of the query entry points: runs the windowed path and
 // returns 1 (its result in *rc) for a batch of at least 2^24 keys against a
-// pilot array of 2 to 8 windows of 72 MiB with aligned buffers; else returns 0 and the
+// pilot array of 2 to 6 automatic windows with aligned buffers; else returns 0 and the
 // caller runs the single pass (also when the scratch cannot be allocated).
 int try_windowed(const mphf *m, const uint64_t *keys, uint64_t count, void *out, int mode, const void *table,
                  cudaStream_t s, int *rc);

@@ -17,6 +17,19 @@ namespace ptrhash {
 constexpr int kThreads = 256;
 constexpr int kKeysPerThread = 8;
 
+// A launch of `blocks` 256-thread CTAs that would not fill one wave at 4
+// CTAs per SM runs as twice as many 128-thread CTAs instead.
+static bool small_batch(uint64_t blocks) {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        sms[dev] = 0;
+        return false;
+    }
+    return blocks < (uint64_t)sms[dev] * 4;
+}
+
 template <int GAMMA>
 __device__ __forceinline__ uint64_t bucket_of(const View &v, uint64_t h, uint64_t &part) {
     part = mul_hi(v.P, h);
@@ -75,18 +88,21 @@ query_u64_wide_kernel(const View v, const uint64_t *__restrict__ keys, const uin
 }
 
 // VEC: keys 16-byte and out 8-byte aligned; pairs of keys per load / store.
-template <int GAMMA, int REDUCE, int REMAP, bool PHF, bool VEC>
-__global__ void __launch_bounds__(kThreads, 4)
+// TPB threads per CTA: 256, or 128 for batches that do not fill one wave of
+// 256-thread CTAs (the same 8 K gathers in flight per SM, spread over twice
+// as many CTAs, so the SMs share the one wave more evenly).
+template <int GAMMA, int REDUCE, int REMAP, bool PHF, bool VEC, int TPB = kThreads>
+__global__ void __launch_bounds__(TPB, 1024 / TPB)
 query_u64_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
                  uint32_t *__restrict__ out) {
     constexpr int K = kKeysPerThread;
-    const uint64_t tile = (uint64_t)blockIdx.x * (kThreads * K);
+    const uint64_t tile = (uint64_t)blockIdx.x * (TPB * K);
     uint64_t h[K], part[K], b[K];
     uint32_t p[K];
-    if (VEC && tile + kThreads * K <= count) {
+    if (VEC && tile + TPB * K <= count) {
 #pragma unroll
         for (int j = 0; j < K / 2; j++) {
-            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint64_t i = tile + (uint64_t)j * 2 * TPB + 2 * threadIdx.x;
             const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + i));
             h[2 * j] = v.C * (((uint64_t)kk.y << 32) | kk.x);
             h[2 * j + 1] = v.C * (((uint64_t)kk.w << 32) | kk.z);
@@ -97,7 +113,7 @@ query_u64_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t
         for (int q = 0; q < K; q++) p[q] = __ldg(v.pilots + b[q]);
 #pragma unroll
         for (int j = 0; j < K / 2; j++) {
-            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint64_t i = tile + (uint64_t)j * 2 * TPB + 2 * threadIdx.x;
             uint2 o;
             o.x = slot_value<REDUCE, REMAP, PHF>(v, h[2 * j], part[2 * j], p[2 * j]);
             o.y = slot_value<REDUCE, REMAP, PHF>(v, h[2 * j + 1], part[2 * j + 1], p[2 * j + 1]);
@@ -106,18 +122,18 @@ query_u64_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t
     } else {
 #pragma unroll
         for (int q = 0; q < K; q++) {
-            const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+            const uint64_t i = tile + (uint64_t)q * TPB + threadIdx.x;
             h[q] = v.C * (i < count ? __ldcs(keys + i) : 0ull);
             b[q] = bucket_of<GAMMA>(v, h[q], part[q]);
         }
 #pragma unroll
         for (int q = 0; q < K; q++) {
-            const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+            const uint64_t i = tile + (uint64_t)q * TPB + threadIdx.x;
             p[q] = i < count ? __ldg(v.pilots + b[q]) : 0u;
         }
 #pragma unroll
         for (int q = 0; q < K; q++) {
-            const uint64_t i = tile + (uint64_t)q * kThreads + threadIdx.x;
+            const uint64_t i = tile + (uint64_t)q * TPB + threadIdx.x;
             if (i < count) out[i] = slot_value<REDUCE, REMAP, PHF>(v, h[q], part[q], p[q]);
         }
     }
@@ -129,10 +145,15 @@ static int launch_u64_t(const View &v, const uint64_t *keys, uint64_t count, uin
     const uint64_t blocks = (count + per_block - 1) / per_block;
     if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
     const bool vec = ((uintptr_t)keys % 16 == 0) && ((uintptr_t)out % 8 == 0);
-    if (vec)
+    if (small_batch(blocks)) {
+        const unsigned b2 = (unsigned)(2 * blocks);   // 128-thread CTAs of half the keys
+        if (vec) query_u64_kernel<GAMMA, REDUCE, REMAP, PHF, true, 128><<<b2, 128, 0, s>>>(v, keys, count, out);
+        else query_u64_kernel<GAMMA, REDUCE, REMAP, PHF, false, 128><<<b2, 128, 0, s>>>(v, keys, count, out);
+    } else if (vec) {
         query_u64_kernel<GAMMA, REDUCE, REMAP, PHF, true><<<(unsigned)blocks, kThreads, 0, s>>>(v, keys, count, out);
-    else
+    } else {
         query_u64_kernel<GAMMA, REDUCE, REMAP, PHF, false><<<(unsigned)blocks, kThreads, 0, s>>>(v, keys, count, out);
+    }
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "query_u64 launch");
@@ -318,18 +339,19 @@ int launch_hash_keys(int key_kind, const void *keys, const uint64_t *offsets, ui
 // ----------------------------------------------------- gather roofline probe
 // The same tile shape and key stream as query_u64_kernel; each key picks a
 // uniformly random byte of the table by fast range of a mixed key.
-__global__ void __launch_bounds__(kThreads)
+template <int TPB>
+__global__ void __launch_bounds__(TPB)
 gather_probe_kernel(const uint64_t *__restrict__ keys, const uint64_t count, const uint8_t *__restrict__ table,
                     const uint64_t table_bytes, uint32_t *__restrict__ out) {
     constexpr int K = kKeysPerThread;
     constexpr uint64_t kMix = 0x9E3779B97F4A7C15ull;
-    const uint64_t tile = (uint64_t)blockIdx.x * (kThreads * K);
+    const uint64_t tile = (uint64_t)blockIdx.x * (TPB * K);
     uint64_t idx[K];
     uint32_t p[K];
-    if (tile + kThreads * K <= count) {
+    if (tile + TPB * K <= count) {
 #pragma unroll
         for (int j = 0; j < K / 2; j++) {
-            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint64_t i = tile + (uint64_t)j * 2 * TPB + 2 * threadIdx.x;
             const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + i));
             idx[2 * j] = mul_hi(kMix * (((uint64_t)kk.y << 32) | kk.x), table_bytes);
             idx[2 * j + 1] = mul_hi(kMix * (((uint64_t)kk.w << 32) | kk.z), table_bytes);
@@ -338,11 +360,11 @@ gather_probe_kernel(const uint64_t *__restrict__ keys, const uint64_t count, con
         for (int q = 0; q < K; q++) p[q] = __ldg(table + idx[q]);
 #pragma unroll
         for (int j = 0; j < K / 2; j++) {
-            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint64_t i = tile + (uint64_t)j * 2 * TPB + 2 * threadIdx.x;
             __stcs(reinterpret_cast<uint2 *>(out + i), make_uint2(p[2 * j], p[2 * j + 1]));
         }
     } else {
-        for (uint64_t i = tile + threadIdx.x; i < count; i += kThreads)
+        for (uint64_t i = tile + threadIdx.x; i < count; i += TPB)
             out[i] = __ldg(table + mul_hi(kMix * __ldcs(keys + i), table_bytes));
     }
 }
@@ -352,17 +374,18 @@ gather_probe_kernel(const uint64_t *__restrict__ keys, const uint64_t count, con
 // stream, mphf_bucket_u64), so the gathers hit the same addresses with the
 // same skew; 8 index bytes in and 4 result bytes out per key, as the query.
 // An index outside the table reads nothing and gives 0.
-__global__ void __launch_bounds__(kThreads)
+template <int TPB>
+__global__ void __launch_bounds__(TPB)
 gather_probe_at_kernel(const uint64_t *__restrict__ idx, const uint64_t count, const uint8_t *__restrict__ table,
                        const uint64_t table_bytes, uint32_t *__restrict__ out) {
     constexpr int K = kKeysPerThread;
-    const uint64_t tile = (uint64_t)blockIdx.x * (kThreads * K);
+    const uint64_t tile = (uint64_t)blockIdx.x * (TPB * K);
     uint64_t b[K];
     uint32_t p[K];
-    if (tile + kThreads * K <= count) {
+    if (tile + TPB * K <= count) {
 #pragma unroll
         for (int j = 0; j < K / 2; j++) {
-            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint64_t i = tile + (uint64_t)j * 2 * TPB + 2 * threadIdx.x;
             const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(idx + i));
             b[2 * j] = ((uint64_t)kk.y << 32) | kk.x;
             b[2 * j + 1] = ((uint64_t)kk.w << 32) | kk.z;
@@ -371,11 +394,11 @@ gather_probe_at_kernel(const uint64_t *__restrict__ idx, const uint64_t count, c
         for (int q = 0; q < K; q++) p[q] = b[q] < table_bytes ? (uint32_t)__ldg(table + b[q]) : 0u;
 #pragma unroll
         for (int j = 0; j < K / 2; j++) {
-            const uint64_t i = tile + (uint64_t)j * 2 * kThreads + 2 * threadIdx.x;
+            const uint64_t i = tile + (uint64_t)j * 2 * TPB + 2 * threadIdx.x;
             __stcs(reinterpret_cast<uint2 *>(out + i), make_uint2(p[2 * j], p[2 * j + 1]));
         }
     } else {
-        for (uint64_t i = tile + threadIdx.x; i < count; i += kThreads) {
+        for (uint64_t i = tile + threadIdx.x; i < count; i += TPB) {
             const uint64_t bi = __ldcs(idx + i);
             out[i] = bi < table_bytes ? (uint32_t)__ldg(table + bi) : 0u;
         }
@@ -421,8 +444,13 @@ extern "C" int mphf_gather_probe_at(const uint64_t *idx_dev, uint64_t count, con
     const uint64_t per_block = (uint64_t)kThreads * kKeysPerThread;
     const uint64_t blocks = (count + per_block - 1) / per_block;
     if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
-    gather_probe_at_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(idx_dev, count, table_dev,
-                                                                                table_bytes, out_dev);
+    if (small_batch(blocks))
+        gather_probe_at_kernel<128><<<(unsigned)(2 * blocks), 128, 0, (cudaStream_t)stream>>>(idx_dev, count, table_dev,
+                                                                                          table_bytes, out_dev);
+    else
+        gather_probe_at_kernel<kThreads><<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(idx_dev, count,
+                                                                                            table_dev, table_bytes,
+                                                                                            out_dev);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "gather probe launch");
@@ -439,8 +467,13 @@ extern "C" int mphf_gather_probe(const uint64_t *keys_dev, uint64_t count, const
     const uint64_t per_block = (uint64_t)kThreads * kKeysPerThread;
     const uint64_t blocks = (count + per_block - 1) / per_block;
     if (blocks > 0x7FFFFFFFull) { set_error("too many keys for one launch"); return MPHF_ERR_ARG; }
-    gather_probe_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(keys_dev, count, table_dev,
-                                                                             table_bytes, out_dev);
+    if (small_batch(blocks))
+        gather_probe_kernel<128><<<(unsigned)(2 * blocks), 128, 0, (cudaStream_t)stream>>>(keys_dev, count, table_dev,
+                                                                                       table_bytes, out_dev);
+    else
+        gather_probe_kernel<kThreads><<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(keys_dev, count,
+                                                                                         table_dev, table_bytes,
+                                                                                         out_dev);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MPHF_OK : cuda_fail(e, "gather probe launch");

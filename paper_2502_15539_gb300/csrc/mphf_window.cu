@@ -34,7 +34,6 @@ constexpr int kWinThreads = 256;
 constexpr int kWinFirstKeys = 8;    // keys per thread in the first pass
 constexpr int kWinMidKeys = 16;     // keys per thread in the middle passes
 constexpr int kWinLastKeys = 4;     // keys per thread in the last pass
-constexpr uint64_t kWindowBytesDefault = 72ull << 20;
 constexpr uint64_t kWindowChunkDefault = 1ull << 28;
 constexpr uint64_t kWindowMinKeys = 1ull << 24;
 
@@ -246,20 +245,38 @@ static int run_windows(const View &v, const uint64_t *keys, uint64_t count, void
     return MPHF_OK;
 }
 
+// The automatic window count (measured on GB300, all keys of a structure
+// queried in a random order, per query of n keys):
+//   pilots   86 MB (n = 3e8):   single 1.97 ms, W = 2 1.86
+//           143 MB (n = 5e8):   single 4.07, W = 2 3.50, W = 3 3.74
+//           200 MB (n = 7e8):   single 6.84, W = 2 5.87, W = 3 5.69, W = 4 6.10
+//           286 MB (n = 1e9):   single 12.54, W = 3 9.17, W = 4 9.38, W = 5 9.89
+//           400 MB (n = 1.4e9): single 18.79, W = 3 15.51, W = 4 14.71, W = 5 15.24
+//           572 MB (n = 2e9):   single 30.08, W = 4 24.94, W = 5 24.43, W = 6 25.17, W = 8 27.55
+//          1.29 GB (n = 4.5e9): single 82.8, W = 18 (72 MB windows) 112
+// The best windows hold 70-115 MB, growing with the pilot array (larger
+// arrays pay more middle passes per window saved).  W = ceil(pilots / 100
+// MB), at least 2, is within 3 % of the best at every size above; the
+// rounding rule round(pilots / 110 MB) was 7-16 % slower on the Compact
+// (250 MB, 2 windows of 125 MB: 9.72 ms against 9.05 in 4 windows) and Fast
+// (334 MB of uniformly used buckets, 3 windows of 111 MB: 11.83 against
+// 10.07-10.22) structures at n = 1e9.  Past 6 windows the middle passes' 6
+// bytes per key outweigh the random reads they replace, and at or below
+// 72 MiB the single pass keeps most pilots in L2.
+constexpr uint64_t kWindowAutoMin = 72ull << 20;
+constexpr uint64_t kWindowAutoBytes = 100000000ull;
+constexpr uint64_t kWindowMaxAuto = 6;
+
 uint64_t window_count_for(uint64_t nbkt, uint64_t window_bytes) {
-    if (window_bytes == 0) window_bytes = kWindowBytesDefault;
-    return (nbkt + window_bytes - 1) / window_bytes;
+    if (window_bytes) return (nbkt + window_bytes - 1) / window_bytes;
+    if (nbkt <= kWindowAutoMin) return 1;
+    uint64_t W = (nbkt + kWindowAutoBytes - 1) / kWindowAutoBytes;
+    if (W < 2) W = 2;
+    return W > kWindowMaxAuto ? 1 : W;
 }
 
-// Every middle pass streams 6 bytes per key, so past about 8 windows the
-// passes cost more than the random DRAM reads they replace: at n = 4.5e9
-// (1.29 GB of pilots, 18 windows) the windowed path took 112 ms per 4.5e9 keys
-// against 82.8 ms for the single pass, at n = 1e9 (4 windows) 9.4 against 12.5.
-constexpr uint64_t kWindowMaxAuto = 8;
-
 uint64_t window_plan(const Header &h, uint64_t count) {
-    const uint64_t W = window_count_for(h.P * h.B, 0);
-    return (W >= 2 && W <= kWindowMaxAuto && count >= kWindowMinKeys) ? W : 1;
+    return count >= kWindowMinKeys ? window_count_for(h.P * h.B, 0) : 1;
 }
 
 uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys) {
