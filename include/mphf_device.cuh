@@ -23,6 +23,18 @@ namespace mphf_dev {
 
 __device__ __forceinline__ uint64_t mul_hi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
 
+// The high and low halves of the 128-bit product a b for a < 2^32, from two
+// 32 x 32 -> 64-bit products: a b = A + Bv 2^32 with A = a lo32(b) and Bv =
+// a hi32(b), so the high half is floor((Bv + floor(A / 2^32)) / 2^32), and
+// Bv + floor(A / 2^32) < 2^64 because Bv <= (2^32 - 1)^2.  Every structure the
+// library builds or loads has P, B < 2^32 (mphf_deserialize rejects others),
+// so Eq. partbucket's products hi(P h) and hi(B gamma) take this form.
+__device__ __forceinline__ uint64_t mul_hi_lo_32x64(uint32_t a, uint64_t b, uint64_t &lo) {
+    const uint64_t A = (uint64_t)a * (uint32_t)b, Bv = (uint64_t)a * (uint32_t)(b >> 32);
+    lo = (Bv << 32) + A;
+    return (Bv + (A >> 32)) >> 32;
+}
+
 // gamma on 64-bit fixed point (Sec. 3.3): gamma_1(x) = x, gamma_3(x) =
 // 255/256 (x^2 + x^3)/2 + x/256 with x^2 = hi(x x), x^3 = hi(x^2 x), floors.
 template <int GAMMA>
@@ -198,10 +210,10 @@ __device__ __forceinline__ uint64_t hash_string_global(const uint8_t *bytes, uin
 // that hs reaches with the bucket's pilot.  Between them sits the one random
 // memory access, pilots[bucket].
 __device__ __forceinline__ uint64_t bucket_index(const mphf_view_t &v, uint64_t hb, uint64_t &part) {
-    part = mul_hi(v.P, hb);
-    const uint64_t x = v.P * hb;   // position inside the part, as a fraction of 2^64
+    uint64_t x, unused;
+    part = mul_hi_lo_32x64((uint32_t)v.P, hb, x);   // x: position inside the part, as a fraction of 2^64
     const uint64_t g = v.gamma == MPHF_GAMMA_CUBIC ? bucket_fn<MPHF_GAMMA_CUBIC>(x) : x;
-    return part * v.B + mul_hi(v.B, g);
+    return part * v.B + mul_hi_lo_32x64((uint32_t)v.B, g, unused);
 }
 
 __device__ __forceinline__ uint64_t slot_of_pilot(const mphf_view_t &v, uint64_t hs, uint64_t part, uint32_t pilot) {

@@ -45,10 +45,11 @@ struct BatchHeader {
     uint32_t pad;
 };
 
+// Eq. partbucket with P, B < 2^32 (true of every structure): 32 x 64-bit products.
 __device__ __forceinline__ uint64_t bucket_any(const View &v, uint64_t h, uint64_t &part, bool cubic) {
-    part = mul_hi(v.P, h);
-    const uint64_t x = v.P * h;
-    return part * v.B + mul_hi(v.B, cubic ? bucket_fn<MPHF_GAMMA_CUBIC>(x) : x);
+    uint64_t x, unused;
+    part = mul_hi_lo_32x64((uint32_t)v.P, h, x);
+    return part * v.B + mul_hi_lo_32x64((uint32_t)v.B, cubic ? bucket_fn<MPHF_GAMMA_CUBIC>(x) : x, unused);
 }
 
 __device__ __forceinline__ uint32_t slot_any(const View &v, uint64_t h, uint64_t part, uint32_t pilot, bool pow2,

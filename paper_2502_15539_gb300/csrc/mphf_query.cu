@@ -30,11 +30,12 @@ static bool small_batch(uint64_t blocks) {
     return blocks < (uint64_t)sms[dev] * 4;
 }
 
+// Eq. partbucket with P, B < 2^32 (true of every structure): 32 x 64-bit products.
 template <int GAMMA>
 __device__ __forceinline__ uint64_t bucket_of(const View &v, uint64_t h, uint64_t &part) {
-    part = mul_hi(v.P, h);
-    const uint64_t x = v.P * h;            // lo(P h): position inside the part
-    return part * v.B + mul_hi(v.B, bucket_fn<GAMMA>(x));
+    uint64_t x, unused;
+    part = mul_hi_lo_32x64((uint32_t)v.P, h, x);   // x = lo(P h): position inside the part
+    return part * v.B + mul_hi_lo_32x64((uint32_t)v.B, bucket_fn<GAMMA>(x), unused);
 }
 
 template <int REDUCE, int REMAP, bool PHF>

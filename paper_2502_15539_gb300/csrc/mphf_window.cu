@@ -37,23 +37,12 @@ constexpr int kWinLastKeys = 4;     // keys per thread in the last pass
 constexpr uint64_t kWindowChunkDefault = 1ull << 28;
 constexpr uint64_t kWindowMinKeys = 1ull << 24;
 
-// hi and lo of the 128-bit product a b for a < 2^32, from two 32 x 32 -> 64
-// products: a b = A + Bv 2^32 with A = a lo32(b), Bv = a hi32(b); the high
-// half is floor((Bv + floor(A / 2^32)) / 2^32), and Bv + floor(A / 2^32) <
-// 2^64 because Bv <= (2^32 - 1)^2.
-__device__ __forceinline__ uint64_t hi32x64(uint32_t a, uint64_t b, uint64_t &lo) {
-    const uint64_t A = (uint64_t)a * (uint32_t)b, Bv = (uint64_t)a * (uint32_t)(b >> 32);
-    lo = (Bv << 32) + A;
-    return (Bv + (A >> 32)) >> 32;
-}
-
-// The bucket index of Eq. partbucket with P, B < 2^32: the same values as
-// bucket_of in the single-pass kernel, with cheaper products.
+// The bucket index of Eq. partbucket (32 x 64-bit products, P, B < 2^32).
 template <int GAMMA>
 __device__ __forceinline__ uint64_t window_bucket(const View &v, uint64_t h) {
     uint64_t x, unused;
-    const uint64_t part = hi32x64((uint32_t)v.P, h, x);
-    return part * v.B + hi32x64((uint32_t)v.B, bucket_fn<GAMMA>(x), unused);
+    const uint64_t part = mul_hi_lo_32x64((uint32_t)v.P, h, x);
+    return part * v.B + mul_hi_lo_32x64((uint32_t)v.B, bucket_fn<GAMMA>(x), unused);
 }
 
 __device__ __forceinline__ bool in_window(uint64_t b, uint64_t lo, uint64_t hi) { return b >= lo && b < hi; }
@@ -157,7 +146,7 @@ window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64
     __syncthreads();
     auto value = [&](uint64_t key, uint32_t b, uint32_t pilot) -> uint64_t {
         uint64_t unused;
-        const uint64_t part = v.B == 1 ? b : hi32x64(b, part_magic, unused);
+        const uint64_t part = v.B == 1 ? b : mul_hi_lo_32x64(b, part_magic, unused);
         const uint64_t s = part * v.S + reduce_slot<REDUCE>(v, (v.C * key) ^ hp[pilot]);
         if (OUT == kOutPhf32 || s < v.n) return s;
         const uint64_t j = s - v.n;
