@@ -135,6 +135,9 @@ def test_automatic_path_matches_oracle_on_a_large_batch():
     auto = N.mphf_query_u64(m, q)
     single = N.mphf_query_u64_windowed(m, q, window_bytes=1 << 40)
     assert torch.equal(auto, single)
+    # either side of the 2^24-key threshold of the automatic choice
+    for cnt in ((1 << 24) - 1, 1 << 24):
+        assert torch.equal(N.mphf_query_u64(m, q[:cnt]), single[:cnt])
     idx = W.uniform_index(200_000, q.numel(), 3).cuda()
     ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
     assert np.array_equal(u32(auto[idx]), ref.query_u64(W.as_uint64_numpy(q[idx]), threads=16))
