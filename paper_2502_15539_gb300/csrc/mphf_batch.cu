@@ -86,13 +86,19 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
     constexpr uint32_t TK = 32 * K;
     uint32_t t = lane == 0 ? atomicAdd(&hdr->counter, 1u) : 0u;
     t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    uint32_t lo = 0;   // the request of the warp's previous tile
     while (t < total) {
         const uint32_t tn = lane == 0 ? atomicAdd(&hdr->counter, 1u) : 0u;   // the next tile, in flight
-        // The request owning tile t: the last r with first_tile[r] <= t.
-        uint32_t lo = 0, hi = nreq;   // invariant: first[lo] <= t < first[hi]
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (s_first[mid] <= t) lo = mid; else hi = mid;
+        // The request owning tile t: the last r with first_tile[r] <= t.  A
+        // warp's consecutive tiles mostly fall in one large request, so the
+        // previous request is checked before searching.
+        if (!(s_first[lo] <= t && t < s_first[lo + 1])) {
+            uint32_t a = 0, b = nreq;   // invariant: first[a] <= t < first[b]
+            while (b - a > 1) {
+                const uint32_t mid = (a + b) >> 1;
+                if (s_first[mid] <= t) a = mid; else b = mid;
+            }
+            lo = a;
         }
         const BatchDesc &d = desc[lo];
         const View v = d.v;

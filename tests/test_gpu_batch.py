@@ -128,3 +128,31 @@ def test_batch_refuses_128_bit_string_structures():
     with pytest.raises(N.MphfError) as e:
         N.Batch(4).run(arr, 1)
     assert e.value.code == N.MPHF_ERR_ARG
+
+
+def test_batch_with_empty_requests_between_others(batch_set):
+    """Empty requests own no tile, so several requests start at the same tile
+    index; every tile must still go to the non-empty request that owns it."""
+    N = need_gpu()
+    structs, reqs = batch_set
+    ms = [N.mphf_deserialize(r.serialize()) for r in structs]
+    empty = torch.empty(0, dtype=torch.int64, device="cuda")
+    empty_out = torch.empty(0, dtype=torch.int32, device="cuda")
+    items, outs = [(ms[0], empty, empty_out)], []
+    for i, (m, q) in enumerate(zip(ms, reqs)):
+        out = torch.full((q.numel(),), -1, dtype=torch.int32, device="cuda")
+        items.append((m, q.cuda(), out))
+        outs.append(out)
+        if i % 3 == 1:
+            items += [(m, empty, empty_out)] * 2
+    items.append((ms[-1], empty, empty_out))
+    arr, keep = N.make_requests(items)
+    for cfg in [(2, 128, 1, True), (8, 256, 4, True)]:
+        b = N.Batch(len(items))
+        b.set_config(*cfg)
+        for o in outs:
+            o.fill_(-1)
+        b.run(arr, len(items))
+        torch.cuda.synchronize()
+        for ref, q, out in zip(structs, reqs, outs):
+            assert np.array_equal(u32(out), ref.query_u64(W.as_uint64_numpy(q)))
