@@ -10,13 +10,24 @@
 // it, so every pilot read after the first touch of its line is an L2 hit.
 // The results are those of Eq. partbucket and Eq. slot, key by key, exactly.
 //
-//   pass 0      keys -> bucket index b (u32 stream) and the pilot of keys in
-//               window 0 (u8 stream); the bucket arithmetic runs only here
+//   pass 0      keys -> bucket index b (u32 stream, when a later pass reads
+//               it) and the pilot of keys in window 0 (u8 stream)
 //   pass 1..W-2 (b, carried pilot) -> carried pilot, filling in window w
 //   pass W-1    (key, b, carried pilot) -> the MPHF value (slot, remap)
 //
 // Sequential traffic per key: 13 B in pass 0, 6 B in each middle pass and
 // 17 B in the last, against one random DRAM access in the single pass.
+// The last pass reads the key anyway (Eq. slot needs h), so it can compute
+// the part and bucket again instead of reading b: 4 B per key less in the
+// last pass, and 4 B less in pass 0 when W = 2 (no middle pass reads b).
+// That pays where the bucket arithmetic is cheap or hidden: gamma_1 (the
+// identity; Fast parameters at n = 1e9, 4 windows: 9.93 against 10.48 ms)
+// and the fused lookup, whose last pass waits on random table reads (29.6
+// against 30.1 ms).  With gamma_3 the two dependent 64-bit high products sit
+// between the key load and the pilot read of a pass that already runs at the
+// DRAM limit: 9.71 against 9.19 ms at n = 1e9 (3 windows), 2.02 against 1.85
+// ms at n = 3e8 (2 windows), and 40 registers or 8 keys per thread were
+// slower still.
 // Keys are processed in chunks of at most 2^28, so the scratch streams (6 B
 // per key of a chunk, 1.6 GB) are bounded; every chunk re-reads the pilot
 // windows once (286 MB per 2^28 keys at n = 1e9, about 1 B per key).
@@ -37,18 +48,25 @@ constexpr int kWinLastKeys = 4;     // keys per thread in the last pass
 constexpr uint64_t kWindowChunkDefault = 1ull << 28;
 constexpr uint64_t kWindowMinKeys = 1ull << 24;
 
-// The bucket index of Eq. partbucket (32 x 64-bit products, P, B < 2^32).
+// The part and bucket index of Eq. partbucket (32 x 64-bit products, P, B < 2^32).
+template <int GAMMA>
+__device__ __forceinline__ uint64_t window_bucket(const View &v, uint64_t h, uint64_t &part) {
+    uint64_t x, unused;
+    part = mul_hi_lo_32x64((uint32_t)v.P, h, x);
+    return part * v.B + mul_hi_lo_32x64((uint32_t)v.B, bucket_fn<GAMMA>(x), unused);
+}
+
 template <int GAMMA>
 __device__ __forceinline__ uint64_t window_bucket(const View &v, uint64_t h) {
-    uint64_t x, unused;
-    const uint64_t part = mul_hi_lo_32x64((uint32_t)v.P, h, x);
-    return part * v.B + mul_hi_lo_32x64((uint32_t)v.B, bucket_fn<GAMMA>(x), unused);
+    uint64_t part;
+    return window_bucket<GAMMA>(v, h, part);
 }
 
 __device__ __forceinline__ bool in_window(uint64_t b, uint64_t lo, uint64_t hi) { return b >= lo && b < hi; }
 
-// Pass 0: bucket index of every key, and the pilot of the keys in [blo, bhi).
-template <int GAMMA>
+// Pass 0: the pilot of the keys in [blo, bhi), and the bucket index of every
+// key when STORE_B.
+template <int GAMMA, bool STORE_B>
 __global__ void __launch_bounds__(kWinThreads, 5)
 window_first_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
                     uint32_t *__restrict__ b32, uint8_t *__restrict__ q, const uint64_t blo, const uint64_t bhi) {
@@ -57,7 +75,7 @@ window_first_kernel(const View v, const uint64_t *__restrict__ keys, const uint6
     if (tile + kWinThreads * K > count) {
         for (uint64_t i = tile + threadIdx.x; i < count; i += kWinThreads) {
             const uint64_t b = window_bucket<GAMMA>(v, v.C * __ldcs(keys + i));
-            b32[i] = (uint32_t)b;
+            if (STORE_B) b32[i] = (uint32_t)b;
             q[i] = in_window(b, blo, bhi) ? __ldg(v.pilots + b) : 0;
         }
         return;
@@ -76,7 +94,7 @@ window_first_kernel(const View v, const uint64_t *__restrict__ keys, const uint6
 #pragma unroll
     for (int j = 0; j < K / 2; j++) {
         const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
-        __stcs(reinterpret_cast<uint2 *>(b32 + i), make_uint2((uint32_t)b[2 * j], (uint32_t)b[2 * j + 1]));
+        if (STORE_B) __stcs(reinterpret_cast<uint2 *>(b32 + i), make_uint2((uint32_t)b[2 * j], (uint32_t)b[2 * j + 1]));
         __stcs(reinterpret_cast<unsigned short *>(q + i), (unsigned short)(p[2 * j] | (p[2 * j + 1] << 8)));
     }
 }
@@ -114,7 +132,9 @@ window_mid_kernel(const uint8_t *__restrict__ pilots, const uint32_t *__restrict
 }
 
 // Last pass: the value of every key (Eq. slot, Sec. 3.4 remap), written in
-// one of the output forms below.  The part is b / B, taken as hi(b M) with
+// one of the output forms below.  With RECOMPUTE the part and bucket come
+// from the key (Eq. partbucket) and b32 is not read; otherwise the part is
+// b / B, taken as hi(b M) with
 // M = ceil(2^64 / B), exact for b, B < 2^32 (the error b (M - 2^64 / B) /
 // 2^64 < 2^-32 < 1 / B cannot carry the quotient over an integer).
 // hp(p) = C (p xor seed) comes from a table of the 256 pilot values in
@@ -132,8 +152,15 @@ template <int OUT> struct WindowOut { using T = uint32_t; };
 template <> struct WindowOut<kOutWide64> { using T = unsigned long long; };
 template <> struct WindowOut<kOutTable8> { using T = unsigned long long; };
 
-template <int REDUCE, int REMAP, int OUT>
-__global__ void __launch_bounds__(kWinThreads, 8)
+// Whether the last pass computes the bucket again (see the traffic note at
+// the top of this file).
+template <int GAMMA, int OUT>
+constexpr bool kRecomputeBucket = GAMMA == MPHF_GAMMA_LINEAR || OUT == kOutTable4 || OUT == kOutTable8;
+
+// 8 resident CTAs (32 registers) for 32-bit values; the 64-bit and table
+// forms keep more live values per key and take 6 (40 registers, no spill).
+template <int GAMMA, int REDUCE, int REMAP, int OUT>
+__global__ void __launch_bounds__(kWinThreads, OUT == kOutMphf32 || OUT == kOutPhf32 ? 8 : 6)
 window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64_t count,
                    const uint32_t *__restrict__ b32, const uint8_t *__restrict__ qin,
                    typename WindowOut<OUT>::T *__restrict__ out, const uint64_t blo, const uint64_t bhi,
@@ -144,10 +171,9 @@ window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64
     __shared__ uint64_t hp[256];
     hp[threadIdx.x] = v.C * ((uint64_t)threadIdx.x ^ v.seed);   // kWinThreads == 256
     __syncthreads();
-    auto value = [&](uint64_t key, uint32_t b, uint32_t pilot) -> uint64_t {
-        uint64_t unused;
-        const uint64_t part = v.B == 1 ? b : mul_hi_lo_32x64(b, part_magic, unused);
-        const uint64_t s = part * v.S + reduce_slot<REDUCE>(v, (v.C * key) ^ hp[pilot]);
+    constexpr bool kRecompute = kRecomputeBucket<GAMMA, OUT>;
+    auto value = [&](uint64_t h, uint64_t part, uint32_t pilot) -> uint64_t {
+        const uint64_t s = part * v.S + reduce_slot<REDUCE>(v, h ^ hp[pilot]);
         if (OUT == kOutPhf32 || s < v.n) return s;
         const uint64_t j = s - v.n;
         if constexpr (REMAP == kRemapClef) {
@@ -162,33 +188,55 @@ window_last_kernel(const View v, const uint64_t *__restrict__ keys, const uint64
         if constexpr (OUT == kOutTable4 || OUT == kOutTable8) return __ldcs(table + val);
         else return (T)val;
     };
+    // The part of bucket b (b < 2^32), from the bucket stream's value.
+    auto part_of = [&](uint64_t b) -> uint64_t {
+        uint64_t unused;
+        return v.B == 1 ? b : mul_hi_lo_32x64((uint32_t)b, part_magic, unused);
+    };
     const uint64_t tile = (uint64_t)blockIdx.x * (kWinThreads * K);
     if (tile + kWinThreads * K > count) {
         for (uint64_t i = tile + threadIdx.x; i < count; i += kWinThreads) {
-            const uint32_t b = b32[i];
-            out[i] = emit(value(__ldcs(keys + i), b, in_window(b, blo, bhi) ? __ldg(v.pilots + b) : qin[i]));
+            const uint64_t h = v.C * __ldcs(keys + i);
+            uint64_t part, b;
+            if constexpr (kRecompute) b = window_bucket<GAMMA>(v, h, part);
+            else { b = b32[i]; part = part_of(b); }
+            out[i] = emit(value(h, part, in_window(b, blo, bhi) ? __ldg(v.pilots + b) : qin[i]));
         }
         return;
     }
-    uint64_t k[K];
-    uint32_t b[K], p[K], c[K / 2];
+    // kh holds h = C k when the bucket is computed again (it is needed ahead
+    // of the pilot reads), else the key, whose product is formed after them
+    // (measured: each order is the faster one for its form).
+    uint64_t kh[K], part[K], b[K];
+    uint32_t p[K], c[K / 2];
+    const uint64_t mul = kRecompute ? v.C : 1;
 #pragma unroll
     for (int j = 0; j < K / 2; j++) {
         const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
         const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + i));
-        k[2 * j] = ((uint64_t)kk.y << 32) | kk.x;
-        k[2 * j + 1] = ((uint64_t)kk.w << 32) | kk.z;
-        const uint2 bb = __ldcs(reinterpret_cast<const uint2 *>(b32 + i));
-        b[2 * j] = bb.x;
-        b[2 * j + 1] = bb.y;
+        kh[2 * j] = mul * (((uint64_t)kk.y << 32) | kk.x);
+        kh[2 * j + 1] = mul * (((uint64_t)kk.w << 32) | kk.z);
+        if constexpr (!kRecompute) {
+            const uint2 bb = __ldcs(reinterpret_cast<const uint2 *>(b32 + i));
+            b[2 * j] = bb.x;
+            b[2 * j + 1] = bb.y;
+        }
         c[j] = __ldcs(reinterpret_cast<const unsigned short *>(qin + i));
+    }
+    if constexpr (kRecompute) {
+#pragma unroll
+        for (int q = 0; q < K; q++) b[q] = window_bucket<GAMMA>(v, kh[q], part[q]);
     }
 #pragma unroll
     for (int q = 0; q < K; q++)
         p[q] = in_window(b[q], blo, bhi) ? (uint32_t)__ldg(v.pilots + b[q]) : (c[q >> 1] >> (8 * (q & 1))) & 0xFFu;
+    if constexpr (!kRecompute) {
+#pragma unroll
+        for (int q = 0; q < K; q++) part[q] = part_of(b[q]);
+    }
     T r[K];
 #pragma unroll
-    for (int q = 0; q < K; q++) r[q] = emit(value(k[q], b[q], p[q]));
+    for (int q = 0; q < K; q++) r[q] = emit(value(kRecompute ? kh[q] : v.C * kh[q], part[q], p[q]));
 #pragma unroll
     for (int j = 0; j < K / 2; j++) {
         const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
@@ -216,12 +264,14 @@ static int run_windows(const View &v, const uint64_t *keys, uint64_t count, void
         uint8_t *qi = qa, *qo = qb;
         for (uint64_t w = 0; w < W; w++) {
             const uint64_t blo = nbkt * w / W, bhi = nbkt * (w + 1) / W;
-            if (w == 0)
-                window_first_kernel<GAMMA><<<first_blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qo, blo, bhi);
+            if (w == 0 && (W > 2 || !kRecomputeBucket<GAMMA, OUT>))
+                window_first_kernel<GAMMA, true><<<first_blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qo, blo, bhi);
+            else if (w == 0)
+                window_first_kernel<GAMMA, false><<<first_blocks, kWinThreads, 0, s>>>(v, keys + c0, cnt, b32, qo, blo, bhi);
             else if (w + 1 < W)
                 window_mid_kernel<<<mid_blocks, kWinThreads, 0, s>>>(v.pilots, b32, cnt, qi, qo, blo, bhi);
             else
-                window_last_kernel<REDUCE, REMAP, OUT><<<last_blocks, kWinThreads, 0, s>>>(
+                window_last_kernel<GAMMA, REDUCE, REMAP, OUT><<<last_blocks, kWinThreads, 0, s>>>(
                     v, keys + c0, cnt, b32, qi, out + c0, blo, bhi, part_magic, table);
             count_launch();
             const cudaError_t e = cudaGetLastError();
