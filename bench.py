@@ -528,6 +528,16 @@ def run_fused(args, m, q, idx, stream, time_steps, remapped):
     one_ms = statistics.mean(time_steps(run_one, args.steps))
     two_ms = statistics.mean(time_steps(run_two, args.steps))
     same = bool(torch.equal(fused_out, two_out))
+    # The table reads alone: one byte of each result's 4-byte table entry, in
+    # the query's order (idx holds the results of the last two-pass run), with
+    # the same 8 B in and 4 B out per key and none of the query's work.
+    tidx = idx.to(torch.int64) * 4
+    probe_out = torch.empty(mq, dtype=torch.int32, device=q.device)
+    run_tp = lambda: N.mphf_gather_probe_at(tidx, table.data_ptr(), 4 * n, probe_out, stream=stream)
+    for _ in range(args.warmup):
+        run_tp()
+    table_probe_ms = statistics.mean(time_steps(run_tp, args.steps))
+    del tidx, probe_out
     # 8 (key) + 4 (result) + 32 (pilot sector) + 32 (table sector) + 64 per remapped key.
     alg = mq * (8 + 4 + 32 + 32) + remapped * 64
     del table, fused_out, two_out
@@ -538,6 +548,10 @@ def run_fused(args, m, q, idx, stream, time_steps, remapped):
                          "peak_kind": peak_kind, "alg_bytes_per_key": alg / mq},
             "fused_ms": one_ms, "fused_queries_per_s": mq / (one_ms / 1e3),
             "two_pass_ms": two_ms, "speedup": two_ms / one_ms, "outputs_identical": same,
+            "gather_roofline": {"probe_ms": table_probe_ms, "frac": table_probe_ms / one_ms,
+                                "probe": "mphf_gather_probe_at: the lookup's table reads alone (each result's "
+                                         "table entry, in query order, 8 B in, 4 B out per key)",
+                                "rest_ms": one_ms - table_probe_ms},
             "fused_alg_bytes_per_key": alg / mq, "fused_achieved_gbs": alg / (one_ms / 1e3) / 1e9,
             "two_pass": "mphf_query_u64 into an int32 index array, then torch.index_select"}
 
@@ -604,7 +618,23 @@ def run_wide(args, dev, stream):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
+    # Matched probe: the query's own pilot reads (the bucket index of every
+    # key of the same stream, gathered from the structure's pilot array),
+    # without the hashing, slot and remap arithmetic; 8 B in and 4 B out per
+    # key against the query's 8 B in and 8 B out.
+    bidx = N.mphf_bucket_u64(m, keys)
     del keys
+    probe_out = torch.empty(n, dtype=torch.int32, device=dev)
+    pilots_ptr = N.mphf_device_view(m).pilots
+    run_p = lambda: N.mphf_gather_probe_at(bidx, pilots_ptr, info["pilot_bytes"], probe_out, stream=stream)
+    run_p()   # warm-up
+    a.record(stream)
+    for _ in range(steps):
+        run_p()
+    b.record(stream)
+    torch.cuda.synchronize()
+    probe_ms = a.elapsed_time(b) / steps
+    del bidx, probe_out
     bijective = False
     if int(out.min().item()) >= 0 and int(out.max().item()) < n:   # in range: the fill stays in bounds
         seen = torch.zeros(n, dtype=torch.uint8, device=dev)
@@ -621,7 +651,10 @@ def run_wide(args, dev, stream):
                          "peak_kind": peak_kind, "alg_bytes_per_key": alg},
             "P": info["P"], "S": info["S"], "bits_per_key": info["bits_per_key"],
             "build_ms": info["build_ms"], "build_ns_per_key": 1e6 * info["build_ms"] / n,
-            "query_ms": ms, "queries_per_s": n / (ms / 1e3), "output_bijective": bijective}
+            "query_ms": ms, "queries_per_s": n / (ms / 1e3), "output_bijective": bijective,
+            "gather_roofline": {"probe_ms": probe_ms, "frac": probe_ms / ms,
+                                "probe": "mphf_gather_probe_at: the query's own pilot reads (mphf_bucket_u64 "
+                                         "of the same key stream) from the structure's pilot array"}}
 
 
 def run_batched(args, dev, stream):
