@@ -143,14 +143,22 @@ def test_automatic_path_matches_oracle_on_a_large_batch():
     assert np.array_equal(u32(auto[idx]), ref.query_u64(W.as_uint64_numpy(q[idx]), threads=16))
 
 
-def test_phf_wide_and_lookup_take_the_windowed_path_with_the_same_values():
+@pytest.mark.parametrize("params", [{"remap": O.REMAP_VEC},
+                                    {"lam": 3.0, "gamma": O.GAMMA_LINEAR, "remap": O.REMAP_VEC}],
+                         ids=["gamma3", "gamma1"])
+def test_phf_wide_and_lookup_take_the_windowed_path_with_the_same_values(params):
     """The PHF query (slots), the 64-bit query and the fused lookup choose the
     windowed path like mphf_query_u64: on a 3e8-key structure and a 2^25-key
-    batch each must equal its single-pass result and the oracle."""
+    batch each must equal its single-pass result and the oracle.  Both
+    structures have two windows; with gamma_1 every last pass computes the
+    bucket from the key and the first pass writes no bucket stream, with
+    gamma_3 only the lookup's does."""
     N = need_gpu()
     n = 3 * 10**8
     keys = W.u64_keys(n, 13, device="cuda")
-    m = N.mphf_build(keys, N.mphf_default_params(remap=O.REMAP_VEC))
+    m = N.mphf_build(keys, N.mphf_default_params(**params))
+    info = N.mphf_info(m)
+    assert info["pilot_bytes"] > 72 << 20 and -(-info["pilot_bytes"] // 100_000_000) <= 2
     q = torch.cat([keys[:(1 << 25) - 1000], W.nonmember_u64_keys(1000, n, 13, device="cuda")]).contiguous()
     del keys
     torch.cuda.empty_cache()
