@@ -110,6 +110,28 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
             const uint64_t *keys = static_cast<const uint64_t *>(d.keys);
             uint64_t h[K], part[K], b[K];
             uint32_t p[K];
+            // A full tile whose keys are 16-byte and outputs 8-byte aligned:
+            // lane l takes the key pairs base + 64 j + 2 l (+1), loaded as one
+            // uint4 and stored as one uint2, with no per-key bounds checks.
+            if (base + TK <= count && ((reinterpret_cast<uintptr_t>(keys + base) | (reinterpret_cast<uintptr_t>(d.out + base) & 7)) & 15) == 0) {
+#pragma unroll
+                for (int j = 0; j < K / 2; j++) {
+                    const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + base + 64u * j + 2 * lane));
+                    h[2 * j] = v.C * (((uint64_t)kk.y << 32) | kk.x);
+                    h[2 * j + 1] = v.C * (((uint64_t)kk.w << 32) | kk.z);
+                }
+#pragma unroll
+                for (int q = 0; q < K; q++) b[q] = bucket_any(v, h[q], part[q], cubic);
+#pragma unroll
+                for (int q = 0; q < K; q++) p[q] = __ldg(v.pilots + b[q]);
+#pragma unroll
+                for (int j = 0; j < K / 2; j++)
+                    __stcs(reinterpret_cast<uint2 *>(d.out + base + 64u * j + 2 * lane),
+                           make_uint2(slot_any(v, h[2 * j], part[2 * j], p[2 * j], pow2, remap),
+                                      slot_any(v, h[2 * j + 1], part[2 * j + 1], p[2 * j + 1], pow2, remap)));
+                t = __shfl_sync(0xFFFFFFFFu, tn, 0);
+                continue;
+            }
 #pragma unroll
             for (int q = 0; q < K; q++) {
                 const uint64_t i = base + 32u * q + lane;

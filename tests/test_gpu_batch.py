@@ -156,3 +156,33 @@ def test_batch_with_empty_requests_between_others(batch_set):
         torch.cuda.synchronize()
         for ref, q, out in zip(structs, reqs, outs):
             assert np.array_equal(u32(out), ref.query_u64(W.as_uint64_numpy(q)))
+
+
+def test_batch_with_unaligned_keys_and_outputs(batch_set):
+    """Full tiles take the paired 16-byte key loads only when a request's keys
+    are 16-byte and its outputs 8-byte aligned; views one element into their
+    buffers (8-byte aligned keys, 4-byte aligned outputs) take the checked
+    per-key path and must give the same values."""
+    N = need_gpu()
+    structs, reqs = batch_set
+    ms = [N.mphf_deserialize(r.serialize()) for r in structs]
+    items, outs, keep_bufs = [], [], []
+    for i, (m, q) in enumerate(zip(ms, reqs)):
+        kbuf = torch.empty(q.numel() + 1, dtype=torch.int64, device="cuda")
+        obuf = torch.full((q.numel() + 1,), -1, dtype=torch.int32, device="cuda")
+        ks = kbuf[1:] if i % 2 else kbuf[:-1]
+        os_ = obuf[1:] if i % 3 else obuf[:-1]
+        ks.copy_(q.cuda())
+        items.append((m, ks, os_))
+        outs.append(os_)
+        keep_bufs += [kbuf, obuf]
+    arr, keep = N.make_requests(items)
+    for cfg in [(4, 512, 4, True), (2, 128, 1, True)]:
+        b = N.Batch(len(items))
+        b.set_config(*cfg)
+        for o in outs:
+            o.fill_(-1)
+        b.run(arr, len(items))
+        torch.cuda.synchronize()
+        for ref, q, out in zip(structs, reqs, outs):
+            assert np.array_equal(u32(out), ref.query_u64(W.as_uint64_numpy(q)))
