@@ -324,7 +324,8 @@ int mphf_batch_get_config(const mphf_batch_t *b, mphf_batch_config *c);
 /* Times every launch shape on this batch (best of 3 runs after a warm-up),
  * keeps the fastest, and writes it to *best (may be NULL).  With a non-NULL
  * cache_path the choice is looked up in / appended to that JSON-lines file,
- * keyed by key kind, decade of the total key count and SM count.
+ * keyed by key kind, decade of the total key count, SM count and the
+ * library's build time (a rebuilt library tunes again).
  * Synchronous. */
 int mphf_batch_autotune(mphf_batch_t *b, const mphf_request *reqs, uint32_t nreq, void *stream,
                         const char *cache_path, mphf_batch_config *best);

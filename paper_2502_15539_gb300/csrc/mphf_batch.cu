@@ -113,7 +113,9 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
             // A full tile whose keys are 16-byte and outputs 8-byte aligned:
             // lane l takes the key pairs base + 64 j + 2 l (+1), loaded as one
             // uint4 and stored as one uint2, with no per-key bounds checks.
-            if (base + TK <= count && ((reinterpret_cast<uintptr_t>(keys + base) | (reinterpret_cast<uintptr_t>(d.out + base) & 7)) & 15) == 0) {
+            const bool paired = base + TK <= count &&
+                                ((reinterpret_cast<uintptr_t>(keys + base) | (reinterpret_cast<uintptr_t>(d.out + base) & 7)) & 15) == 0;
+            if (paired) {
 #pragma unroll
                 for (int j = 0; j < K / 2; j++) {
                     const uint4 kk = __ldcs(reinterpret_cast<const uint4 *>(keys + base + 64u * j + 2 * lane));
@@ -129,24 +131,23 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
                     __stcs(reinterpret_cast<uint2 *>(d.out + base + 64u * j + 2 * lane),
                            make_uint2(slot_any(v, h[2 * j], part[2 * j], p[2 * j], pow2, remap),
                                       slot_any(v, h[2 * j + 1], part[2 * j + 1], p[2 * j + 1], pow2, remap)));
-                t = __shfl_sync(0xFFFFFFFFu, tn, 0);
-                continue;
-            }
+            } else {   // a ragged or unaligned tile: lane l takes keys base + 32 q + l
 #pragma unroll
-            for (int q = 0; q < K; q++) {
-                const uint64_t i = base + 32u * q + lane;
-                h[q] = v.C * (i < count ? __ldcs(keys + i) : 0ull);
-                b[q] = bucket_any(v, h[q], part[q], cubic);
-            }
+                for (int q = 0; q < K; q++) {
+                    const uint64_t i = base + 32u * q + lane;
+                    h[q] = v.C * (i < count ? __ldcs(keys + i) : 0ull);
+                    b[q] = bucket_any(v, h[q], part[q], cubic);
+                }
 #pragma unroll
-            for (int q = 0; q < K; q++) {
-                const uint64_t i = base + 32u * q + lane;
-                p[q] = i < count ? __ldg(v.pilots + b[q]) : 0u;
-            }
+                for (int q = 0; q < K; q++) {
+                    const uint64_t i = base + 32u * q + lane;
+                    p[q] = i < count ? __ldg(v.pilots + b[q]) : 0u;
+                }
 #pragma unroll
-            for (int q = 0; q < K; q++) {
-                const uint64_t i = base + 32u * q + lane;
-                if (i < count) __stcs(d.out + i, slot_any(v, h[q], part[q], p[q], pow2, remap));
+                for (int q = 0; q < K; q++) {
+                    const uint64_t i = base + 32u * q + lane;
+                    if (i < count) __stcs(d.out + i, slot_any(v, h[q], part[q], p[q], pow2, remap));
+                }
             }
         } else {
             // Strings: groups of 32 consecutive strings through the warp's stage.
@@ -422,8 +423,11 @@ int mphf_batch_autotune(mphf_batch_t *b, const mphf_request *reqs, uint32_t nreq
         if (reqs[i].offsets_dev) kind = MPHF_KEY_BYTES;
     }
     const int decade = total ? (int)floor(log10((double)total)) : 0;
-    char key[96];
-    snprintf(key, sizeof(key), "\"kind\": %d, \"log10_keys\": %d, \"sms\": %d", kind, decade, b->sms);
+    // The build stamp keeps a shape measured on another build of the kernel
+    // (whose best shape may differ) from being reused.
+    char key[192];
+    snprintf(key, sizeof(key), "\"kind\": %d, \"log10_keys\": %d, \"sms\": %d, \"build\": \"%s %s\"", kind, decade,
+             b->sms, __DATE__, __TIME__);
     if (cache_path) {
         FILE *f = fopen(cache_path, "r");
         if (f) {
