@@ -9,9 +9,10 @@ The C source (``ptrhash_oracle.c``) restates the PtrHash paper: Eq. partbucket
 and Eq. slot (Sec. 3.1), the greedy + hash-evict construction (Sec. 3.2),
 the bucket functions gamma_1 / gamma_3 (Sec. 3.3) and remapping with
 CacheLineEF (Sec. 3.4, Eq. clef).  The string hash is the project's own
-definition: its finishing mixer is pinned to SplitMix64's published outputs,
-its per-word fold is parity unpinned against external values (pinned by
-properties).
+definition.  Its finishing mixer is pinned to SplitMix64's published outputs.
+Its per-word fold and sum are pinned to the same outputs through words whose
+fold has a closed form (inputs 0, 1 and 2^63); at other inputs the fold is
+checked by properties only.
 """
 from __future__ import annotations
 

@@ -72,8 +72,8 @@ void orc_part_bucket(const orc_layout *L, int gamma, uint64_t h,
 }
 
 /* String keys.  The paper uses GxHash, which it does not define; this is the
- * project's own 64-bit string hash (the fold is parity unpinned against
- * external values; the finishing mixer is pinned to SplitMix64's outputs):
+ * project's own 64-bit string hash (the finishing mixer, and the fold and
+ * sum at word inputs 0, 1 and 2^63, are pinned to SplitMix64's outputs):
  *   fold(x) = high 64 bits xor low 64 bits of the 128-bit product x * K3
  *   w_j     = little-endian u64 of bytes [8j, 8j+8), zero-padded past len
  *   acc     = sum_j fold(w_j xor (seed + j * K1))             (mod 2^64)

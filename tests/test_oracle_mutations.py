@@ -38,6 +38,12 @@ MUTATIONS = {
     "string mixer with a wrong shift": ("    z ^= z >> 27;\n", "    z ^= z >> 28;\n"),
     "string hash drops the seed from the finish": ("return str_mix(acc ^ (len * K2) ^ seed);",
                                                    "return str_mix(acc ^ (len * K2));"),
+    "string fold drops the high half": ("return (uint64_t)(p >> 64) ^ (uint64_t)p;", "return (uint64_t)p;"),
+    "string words combined with xor": ("acc += str_fold(w ^ (seed + j * K1), K3);", "acc ^= str_fold(w ^ (seed + j * K1), K3);"),
+    "string word tweak off by one word": ("acc += str_fold(w ^ (seed + j * K1), K3);",
+                                          "acc += str_fold(w ^ (seed + (j + 1) * K1), K3);"),
+    "string words read big-endian": ("w |= byte << (8 * b);", "w |= byte << (56 - 8 * b);"),
+    "string hash drops the length": ("return str_mix(acc ^ (len * K2) ^ seed);", "return str_mix(acc ^ seed);"),
     "x mod S layout keeps an even S": ("            if (S % 2 == 0) S += 1;\n",
                                       "            if (is_pow2(S)) S += 1;\n"),
     "128-bit query buckets by the low half": ("orc_part_bucket(&m->L, m->gamma, hb, &part, &b);",

@@ -431,6 +431,35 @@ def test_empty_string_hash_is_the_splitmix64_mixer_of_the_seed():
         assert hi == want
 
 
+def test_string_hash_words_are_pinned_by_splitmix64():
+    """The per-word part of the string hash, pinned through the SplitMix64 outputs
+    (tests/golden/splitmix64_seed0.txt).  For word inputs 0, 1 and 2^63 the fold's
+    128-bit product x K collapses to shifts: fold(0) = 0, fold(1) = K and, K being
+    odd, fold(2^63) = (K >> 1) xor 2^63.  Strings are built whose words, xored with
+    their tweaks seed + j K1, are such inputs; the seed is then chosen so that the
+    finisher's input acc xor len K2 xor seed is k * 0x9E3779B97F4A7C15, whose mix
+    is the generator's k-th output.  A wrong word order, tweak, fold half, word
+    combination or length term gives another value.  The high half of the 128-bit
+    hash is checked the same way with its seed xor K4 and its fold constant K5."""
+    K1, K2 = 0x9E3779B97F4A7C15, 0xC2B2AE3D27D4EB4F
+    K3, K4, K5 = 0xA173621FA8385BE3, 0x47523634D9D6709B, 0x2EF8175451B07575
+    le = lambda x: (x & M64).to_bytes(8, "little")
+    for k, want in ((int(r[0]), int(r[1], 16)) for r in golden_rows("splitmix64_seed0.txt")):
+        target = (k * 0x9E3779B97F4A7C15) & M64
+        for K, seed_xor in ((K3, 0), (K5, K4)):
+            cases = (((0,), 0), ((1,), K), ((1 << 63,), (K >> 1) ^ (1 << 63)),
+                     ((1, 1), (2 * K) & M64), ((0, 1, 0), K))
+            for inputs, acc in cases:
+                n = 8 * len(inputs)
+                inner = target ^ acc ^ ((n * K2) & M64)   # the seed inside the word hash
+                s = b"".join(le(x ^ (inner + j * K1)) for j, x in enumerate(inputs))
+                if seed_xor == 0:
+                    assert O.hash_bytes(s, inner) == want, (k, inputs)
+                else:
+                    hi, lo = O.hash_bytes128(s, inner ^ seed_xor)
+                    assert hi == want, (k, inputs)
+
+
 def test_string_hash_properties():
     """Project string hash: depends on every byte, on the length and on the seed."""
     rng = random.Random(9)
