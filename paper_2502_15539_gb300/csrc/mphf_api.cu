@@ -25,7 +25,8 @@ struct mphf {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_q[2] = {}, ev_d2h[2] = {};
     bool owns_device_memory = true;   // false: pilots / remap live in a caller's arena
-    // Scratch of the windowed query (6 bytes per key of a chunk), allocated
+    // Scratch of the windowed query (6 bytes per key of a chunk rounded up
+    // to 16 keys; win_chunk holds that rounded count), allocated
     // on first use and kept; win_done orders its uses on different streams.
     std::mutex win_mu;
     uint8_t *d_win = nullptr;
@@ -441,20 +442,21 @@ int handle_windowed_query(const mphf_t *mc, const uint64_t *keys, uint64_t count
                           const void *table, uint64_t W, uint64_t chunk_keys, cudaStream_t s) {
     mphf_t *m = const_cast<mphf_t *>(mc);   // the scratch is mutable state of a const structure
     const uint64_t chunk = window_chunk_for(count, chunk_keys);
+    const uint64_t cp = window_stream_keys(chunk);   // the scratch holds 6 bytes per padded key
     std::lock_guard<std::mutex> lock(m->win_mu);
-    if (m->win_chunk < chunk) {
+    if (m->win_chunk < cp) {
         if (m->d_win) {   // grow: cudaFree waits for every earlier use
             cudaFree(m->d_win);
             m->d_win = nullptr;
             m->win_chunk = 0;
         }
-        cudaError_t e = cudaMalloc(&m->d_win, 6 * chunk);
+        cudaError_t e = cudaMalloc(&m->d_win, 6 * cp);
         if (e != cudaSuccess) {
             m->d_win = nullptr;
             cudaGetLastError();
             return cuda_fail(e, "windowed query scratch");
         }
-        m->win_chunk = chunk;
+        m->win_chunk = cp;
     }
     if (!m->win_done) {
         cudaError_t e = cudaEventCreateWithFlags(&m->win_done, cudaEventDisableTiming);

@@ -79,6 +79,9 @@ enum : int { kWinMphf32 = 0, kWinPhf32 = 1, kWinWide64 = 2, kWinTable4 = 3, kWin
 uint64_t window_count_for(uint64_t nbkt, uint64_t window_bytes);
 uint64_t window_plan(const Header &h, uint64_t count);
 uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys);
+// Keys per scratch stream for a chunk: the chunk rounded up to 16, so that
+// every stream of the scratch starts 16-byte aligned.
+uint64_t window_stream_keys(uint64_t chunk);
 int window_out_bytes(int mode);
 // Keys 16-byte aligned, out aligned to two elements, P B < 2^32.
 bool window_supported(const Header &h, const uint64_t *keys, const void *out, int out_bytes);

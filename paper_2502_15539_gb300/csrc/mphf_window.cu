@@ -112,22 +112,32 @@ window_mid_kernel(const uint8_t *__restrict__ pilots, const uint32_t *__restrict
         }
         return;
     }
-    uint32_t b[K], p[K], c[K / 2];
+    // Thread t takes keys tile + 4 kWinThreads j + 4 t + e (e < 4): per j one
+    // 16-byte bucket load, one 4-byte carried-pilot load and one 4-byte
+    // store, each warp access 512 or 128 contiguous bytes.  The carried
+    // pilot streams are 16-byte aligned (run_windows lays them out so).
+    uint32_t b[K], c[K / 4];
 #pragma unroll
-    for (int j = 0; j < K / 2; j++) {
-        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
-        const uint2 bb = __ldcs(reinterpret_cast<const uint2 *>(b32 + i));
-        b[2 * j] = bb.x;
-        b[2 * j + 1] = bb.y;
-        c[j] = __ldcs(reinterpret_cast<const unsigned short *>(qin + i));
+    for (int j = 0; j < K / 4; j++) {
+        const uint64_t i = tile + (uint64_t)j * 4 * kWinThreads + 4 * threadIdx.x;
+        const uint4 bb = __ldcs(reinterpret_cast<const uint4 *>(b32 + i));
+        b[4 * j] = bb.x;
+        b[4 * j + 1] = bb.y;
+        b[4 * j + 2] = bb.z;
+        b[4 * j + 3] = bb.w;
+        c[j] = __ldcs(reinterpret_cast<const uint32_t *>(qin + i));
+    }
+    uint32_t o[K / 4] = {};
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const uint32_t carried = (c[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+        const uint32_t p = in_window(b[k], blo, bhi) ? (uint32_t)__ldg(pilots + b[k]) : carried;
+        o[k >> 2] |= p << (8 * (k & 3));
     }
 #pragma unroll
-    for (int k = 0; k < K; k++)
-        p[k] = in_window(b[k], blo, bhi) ? (uint32_t)__ldg(pilots + b[k]) : (c[k >> 1] >> (8 * (k & 1))) & 0xFFu;
-#pragma unroll
-    for (int j = 0; j < K / 2; j++) {
-        const uint64_t i = tile + (uint64_t)j * 2 * kWinThreads + 2 * threadIdx.x;
-        __stcs(reinterpret_cast<unsigned short *>(qout + i), (unsigned short)(p[2 * j] | (p[2 * j + 1] << 8)));
+    for (int j = 0; j < K / 4; j++) {
+        const uint64_t i = tile + (uint64_t)j * 4 * kWinThreads + 4 * threadIdx.x;
+        __stcs(reinterpret_cast<uint32_t *>(qout + i), o[j]);
     }
 }
 
@@ -255,7 +265,8 @@ static int run_windows(const View &v, const uint64_t *keys, uint64_t count, void
     const T *table = static_cast<const T *>(table_v);
     const uint64_t nbkt = v.P * v.B;
     uint32_t *b32 = reinterpret_cast<uint32_t *>(scratch);
-    uint8_t *qa = scratch + 4 * chunk, *qb = qa + chunk;
+    const uint64_t cp = window_stream_keys(chunk);   // 16-byte aligned carried-pilot streams
+    uint8_t *qa = scratch + 4 * cp, *qb = qa + cp;
     for (uint64_t c0 = 0; c0 < count; c0 += chunk) {
         const uint64_t cnt = count - c0 < chunk ? count - c0 : chunk;
         const unsigned first_blocks = (unsigned)((cnt + kWinThreads * kWinFirstKeys - 1) / (kWinThreads * kWinFirstKeys));
@@ -318,6 +329,8 @@ uint64_t window_plan(const Header &h, uint64_t count) {
     return count >= kWindowMinKeys ? window_count_for(h.P * h.B, 0) : 1;
 }
 
+uint64_t window_stream_keys(uint64_t chunk) { return (chunk + 15) & ~15ull; }
+
 uint64_t window_chunk_for(uint64_t count, uint64_t chunk_keys) {
     uint64_t chunk = chunk_keys ? chunk_keys : kWindowChunkDefault;
     const uint64_t even = count + (count & 1);
@@ -357,8 +370,8 @@ static int run_windows_layout(const Header &h, const View &v, const uint64_t *ke
 
 int window_out_bytes(int mode) { return mode == kWinWide64 || mode == kWinTable8 ? 8 : 4; }
 
-// scratch: 6 chunk bytes of device memory (the bucket stream and two
-// carried-pilot streams of one chunk), at least 8-byte aligned.
+// scratch: 6 window_stream_keys(chunk) bytes of device memory (the bucket
+// stream and two carried-pilot streams of one chunk), 16-byte aligned.
 int launch_query_u64_windowed(const Header &h, const View &v, const uint64_t *keys, uint64_t count, void *out,
                               int mode, const void *table, uint64_t W, uint64_t chunk, uint8_t *scratch,
                               cudaStream_t s) {
