@@ -307,7 +307,7 @@ typedef struct mphf_batch mphf_batch_t;
  * structure and size (the paper's query_all over many structures, App. A;
  * no paper counterpart for the multi-structure dispatch).  Owns two staging
  * sets (page-locked host + device descriptor buffers) and their graphs.
- * Default shape: 8 keys per thread, 256 threads, 4 CTAs per SM, graphs on. */
+ * Default shape: 8 keys per thread, 512 threads, 2 CTAs per SM, graphs on. */
 int mphf_batch_create(uint32_t max_requests, mphf_batch_t **out);
 
 /* Evaluates every request; results are identical to mphf_query_u64 /

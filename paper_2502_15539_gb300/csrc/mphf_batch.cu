@@ -170,7 +170,7 @@ batch_query_kernel(const BatchDesc *__restrict__ desc, const uint32_t *__restric
 
 // ----------------------------------------------------------------- host
 struct BatchConfig {
-    int keys_per_thread = 8, threads = 256, blocks_per_sm = 4;
+    int keys_per_thread = 8, threads = 512, blocks_per_sm = 2;
 };
 
 static bool valid_config(const BatchConfig &c) {
