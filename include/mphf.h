@@ -158,9 +158,10 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
  * array is cut into W = ceil(P B / window_bytes) byte ranges, each small
  * enough to stay in L2, and the keys are streamed once per range: the first
  * pass computes every key's bucket (Eq. partbucket) and keeps it in a 32-bit
- * stream, each pass reads the pilots of the keys whose bucket lies in its
- * range, and the last pass computes the slot and remap value (Eq. slot,
- * Sec. 3.4).  Random DRAM reads of the pilot array become L2 hits, at the
+ * stream for the passes that read it, each pass reads the pilots of the keys
+ * whose bucket lies in its range, and the last pass computes the slot and
+ * remap value (Eq. slot, Sec. 3.4); for gamma_1 structures the last pass
+ * computes the bucket again from the key instead of reading the stream.  Random DRAM reads of the pilot array become L2 hits, at the
  * cost of reading the keys twice and 6 bytes of scratch traffic per key and
  * middle pass.  Results equal mphf_query_u64's, key by key.
  *   window_bytes  pilot bytes per range; 0: the automatic W above (which
@@ -168,9 +169,9 @@ int mphf_query_u64(const mphf_t *m, const uint64_t *keys_dev, uint64_t count,
  *                 single-pass kernel.
  *   chunk_keys    keys per chunk (even, at most 2^31; 0: 2^28).  Every chunk
  *                 reads the pilot array once more; the scratch is 6 bytes per
- *                 key of a chunk, owned by the structure (allocated on first
- *                 use, grown when a larger chunk is asked for, freed by
- *                 mphf_free).  Uses of the scratch from different streams are
+ *                 key of a chunk rounded up to 16 keys, owned by the
+ *                 structure (allocated on first use, grown when a larger
+ *                 chunk is asked for, freed by mphf_free).  Uses of the scratch from different streams are
  *                 ordered on the GPU.
  * keys_dev 16-byte and out_dev 8-byte aligned when W >= 2.  Asynchronous on
  * `stream`, except that allocating or growing the scratch synchronizes the
