@@ -115,6 +115,28 @@ def test_autotune_picks_a_valid_shape_and_caches_it(batch_set, tmp_path):
     run_and_check(N, b2, structs, reqs)
 
 
+def test_autotune_ignores_a_shape_cached_by_another_build(batch_set, tmp_path):
+    """The cache key holds the library's build time: an entry written by another
+    build of the kernel (whose best shape may differ) is not reused."""
+    import json
+    N = need_gpu()
+    structs, reqs = batch_set
+    ms = [N.mphf_deserialize(r.serialize()) for r in structs]
+    items = [(m, q.cuda(), torch.empty(q.numel(), dtype=torch.int32, device="cuda")) for m, q in zip(ms, reqs)]
+    arr, keep = N.make_requests(items)
+    cache = tmp_path / "tune.jsonl"
+    N.Batch(64).autotune(arr, len(items), str(cache))
+    entry = json.loads(cache.read_text().splitlines()[0])
+    assert entry["build"]
+    planted = dict(entry, build="Jan  1 2000 00:00:00", keys_per_thread=2, threads=128, blocks_per_sm=1)
+    cache.write_text(json.dumps(planted) + "\n")
+    best = N.Batch(64).autotune(arr, len(items), str(cache))
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 2 and json.loads(lines[1])["build"] == entry["build"]
+    assert (best["keys_per_thread"], best["threads"], best["blocks_per_sm"]) == \
+        (json.loads(lines[1])["keys_per_thread"], json.loads(lines[1])["threads"], json.loads(lines[1])["blocks_per_sm"])
+
+
 def test_batch_refuses_128_bit_string_structures():
     """The batch executor returns 32-bit results through the 64-bit string
     hash only; a structure with the 128-bit hash is refused, not misread."""
