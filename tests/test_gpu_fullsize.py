@@ -124,9 +124,11 @@ def test_u64_past_2_32_keys():
     parts, Appendix B) and the 64-bit-result query over every key.  Checked
     by properties that hold at any size: the results form a bijection onto
     [0, n) (a device bitmap), so no value was cut to 32 bits, and values past
-    2^32 occur.  (The oracle's builder would need minutes at this size; the
-    64-bit query path is compared with the oracle element by element at
-    small n in test_gpu_query.)"""
+    2^32 occur.  A seeded sample of outputs, with positions whose values pass
+    2^32, is compared element by element with the oracle's evaluation of the
+    same GPU-built structure (serialized and read by the oracle; its builder
+    would need minutes at this size).  The 64-bit query path is also
+    compared with the oracle on every key at small n in test_gpu_query.)"""
     N = need_gpu()
     n = 4_500_000_000
     chunk = 1 << 28
@@ -142,6 +144,13 @@ def test_u64_past_2_32_keys():
     torch.cuda.synchronize()
     del keys
     assert int(out.min().item()) >= 0 and int(out.max().item()) == n - 1   # in range: the fill stays in bounds
+    high = torch.nonzero(out >= (1 << 32)).flatten()[:20_000]
+    idx = torch.unique(torch.cat([sample_positions(n, m=200_000).cuda(), high]))
+    got = out[idx].cpu().numpy().view(np.uint64)
+    ref = O.OracleMPHF.deserialize(N.mphf_serialize(m))
+    want = ref.query_u64(W.as_uint64_numpy(W.u64_keys_at(idx, seed=3)), threads=CORES)
+    assert int((got >= (1 << 32)).sum()) > 0 and np.array_equal(got, want.astype(np.uint64))
+    del ref
     assert int((out >= (1 << 32)).sum().item()) == n - (1 << 32)
     seen = torch.zeros(n, dtype=torch.uint8, device="cuda")
     seen.index_fill_(0, out, 1)
