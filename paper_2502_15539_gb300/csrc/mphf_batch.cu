@@ -2,9 +2,10 @@
 //
 // A batch is a list of requests (structure, keys, count, out).  The host
 // turns it into one descriptor per request (the structure's view plus the
-// request's first tile) and the kernel's CTAs pull 2048-key-ish tiles from
-// a global counter until every tile is done, so structures of very
-// different sizes and batches of 1 to 1e6 keys share one launch.  The
+// request's first tile) and the kernel's warps pull tiles of 32 K keys (K
+// keys per lane) from a global counter until every tile is done, so
+// structures of very different sizes and batches of 1 to 1e6 keys share one
+// launch.  The
 // upload of the descriptors, the counter reset and the kernel are captured
 // once into a CUDA graph and replayed for every batch.  Launch shape (keys
 // per thread, threads, CTAs per SM) comes from an autotuner that times the
