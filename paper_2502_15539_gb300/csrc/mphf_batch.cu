@@ -5,11 +5,11 @@
 // request's first tile) and the kernel's warps pull tiles of 32 K keys (K
 // keys per lane) from a global counter until every tile is done, so
 // structures of very different sizes and batches of 1 to 1e6 keys share one
-// launch.  The
-// upload of the descriptors, the counter reset and the kernel are captured
-// once into a CUDA graph and replayed for every batch.  Launch shape (keys
-// per thread, threads, CTAs per SM) comes from an autotuner that times the
-// candidates on a real batch and keeps the winner in a small JSON cache.
+// launch.  The upload of the descriptors, the counter reset and the kernel
+// are captured once into a CUDA graph and replayed for every batch.  Launch
+// shape (keys per lane, threads, CTAs per SM) comes from an autotuner that
+// times the candidates on a real batch and keeps the winner in a small JSON
+// cache.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
