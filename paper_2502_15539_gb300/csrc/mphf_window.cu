@@ -21,9 +21,9 @@
 // the part and bucket again instead of reading b: 4 B per key less in the
 // last pass, and 4 B less in pass 0 when W = 2 (no middle pass reads b).
 // That pays where the bucket arithmetic is cheap or hidden: gamma_1 (the
-// identity; Fast parameters at n = 1e9, 4 windows: 9.93 against 10.48 ms)
-// and the fused lookup, whose last pass waits on random table reads (29.6
-// against 30.1 ms).  With gamma_3 the two dependent 64-bit high products sit
+// identity; Fast parameters at n = 1e9, 4 windows: 9.92 against 10.46 ms on
+// one GPU) and the fused lookup, whose last pass waits on random table reads
+// (27.88 against 28.39 ms).  With gamma_3 the two dependent 64-bit high products sit
 // between the key load and the pilot read of a pass that already runs at the
 // DRAM limit: 9.71 against 9.19 ms at n = 1e9 (3 windows), 2.02 against 1.85
 // ms at n = 3e8 (2 windows), and 40 registers or 8 keys per thread were
@@ -37,13 +37,17 @@ namespace ptrhash {
 
 // Launch shapes (measured at n = 1e9, one 2^28-key chunk per pass: keys per
 // thread / resident CTAs per SM): the first pass 8 / 5 (0.77 ms; 8 / 4 took
-// 0.81, 4 / 8 0.83), the middle passes 16 / 4 (0.40 ms), the last pass 4 / 8
-// (0.95 ms; 8 / 4 took 1.13, 8 / 5 1.03).  The last pass has the most
-// arithmetic per key and the most streams; more resident warps hide its
-// load latency better than more keys per thread.
+// 0.81, 4 / 8 0.83), the last pass 4 / 8 (0.95 ms; 8 / 4 took 1.13, 8 / 5
+// 1.03).  The last pass has the most arithmetic per key and the most
+// streams; more resident warps hide its load latency better than more keys
+// per thread.  The middle passes take 8 keys per thread (27 registers, 8 CTAs
+// per SM): the same time as 16 or 32 at n = 1e9 (3 windows), 14.84 ms
+// against 15.20 (16) and 15.30 (32) at n = 1.4e9 (5 windows).  (With 16 keys
+// per thread the middle pass's top stall was a full queue of memory
+// instructions.)
 constexpr int kWinThreads = 256;
 constexpr int kWinFirstKeys = 8;    // keys per thread in the first pass
-constexpr int kWinMidKeys = 16;     // keys per thread in the middle passes
+constexpr int kWinMidKeys = 8;      // keys per thread in the middle passes
 constexpr int kWinLastKeys = 4;     // keys per thread in the last pass
 constexpr uint64_t kWindowChunkDefault = 1ull << 28;
 constexpr uint64_t kWindowMinKeys = 1ull << 24;

@@ -22,4 +22,4 @@ def test_traffic_record_matches_the_current_query_kernel():
 def test_traffic_record_is_refused_at_another_granularity_or_structure():
     assert bench.recorded_traffic(10**9, 10**9, 32) is None
     assert bench.recorded_traffic(10**8, 10**8, 128) is None   # a smaller structure: other bytes per key
-    assert bench.recorded_traffic(10**9, 2**26, 128) == 62.37 * 2**26
+    assert bench.recorded_traffic(10**9, 2**26, 128) == 62.39 * 2**26
